@@ -1,0 +1,369 @@
+"""Benchmark of the GB300 randUTV library on the paper-shaped 16000 x 16000 workload.
+
+One step = one complete factorization A = U T V^T (every block step: sketch,
+QR of the sketch, right WY update, panel QR, left WY update, b x b SVD) of a
+16000 x 16000 FP64 matrix with the gap spectrum, b = 128, q = 2, U and V formed.
+value = whole-job effective TFLOP/s from the fixed randUTV flop count F (below),
+summed over ranks (one independent factorization per GPU: replicas, weak
+scaling).  Prints ONE JSON line on rank 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                    [--n 16000] [--b 128] [--q 2] [--prec fp64|bf16] [--no-e2e] [--no-cpu]
+
+--impl reference times the CPU oracle (the plain FP64 randUTV used as the
+parity reference) on the host cores, each step a bounded sample of the same
+workload (the same spectrum, b and q at n = 1536).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "randUTV s/factorization & TFLOP/s at n=16000: mixed/learned-q vs FP64, % peak"
+
+
+def randutv_flops(m: int, n: int, b: int, q: int, uv: bool = True) -> float:
+    """Fixed leading-order flop count F of blocked randUTV (the paper gives none).
+
+    Summed over the sketch steps i (n' = n - i b > b), with m' = m - i b:
+      2(1+2q) m' n' b    sketch and power iteration (Sec. 3.2.1)
+      4 m n' b           right WY update of T(:, J2), all m rows (Sec. 5.4)
+      4 m' (n'-b) b      left WY update of T22(:, b+1:) (Sec. 3.2.2)
+      4 n n' b, 4 m m' b right updates of V and U (when formed)
+      2 (m'+n') b^2      the two Householder panels
+    The final block (n' <= b) adds 2 m' n'^2 (+ 4 m m' n' for U).
+    """
+    F = 0.0
+    i = 0
+    while True:
+        mp, np_ = m - i * b, n - i * b
+        if np_ <= 0:
+            break
+        if np_ <= b:
+            F += 2.0 * mp * np_ * np_ + (4.0 * m * mp * np_ if uv else 0.0)
+            break
+        F += 2.0 * (1 + 2 * q) * mp * np_ * b + 4.0 * m * np_ * b + 4.0 * mp * (np_ - b) * b
+        if uv:
+            F += 4.0 * n * np_ * b + 4.0 * m * mp * b
+        F += 2.0 * (mp + np_) * b * b
+        i += 1
+    return F
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[4:8]):
+                if flag.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(n: int, b: int, q: int, kind: str, reps: int = 1):
+    """Time the CPU oracle on one n x n sample of the workload -> (TFLOP/s, seconds, threads)."""
+    import oracle
+    import synthetic
+
+    A = synthetic.test_matrix(n, n, kind, 1, 2)
+    oracle.build()
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.randutv(A, b, q, 0)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return randutv_flops(n, n, b, q) / best / 1e12, best, oracle.num_threads()
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    import synthetic
+
+    n_s = 1536
+    A = synthetic.test_matrix(n_s, n_s, args.spectrum, 1, 2)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.randutv(A, args.b, args.q, 0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.randutv(A, args.b, args.q, 0)
+    dt = (time.perf_counter() - t0) / args.steps
+    F = randutv_flops(n_s, n_s, args.b, args.q)
+    val = F / dt / 1e12
+    sample = "oracle (plain C, OpenMP, FP64) on a %dx%d %s-spectrum matrix, b=%d, q=%d, U and V formed; " \
+             "one factorization per step" % (n_s, n_s, args.spectrum, args.b, args.q)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "randUTV FP64 %dx%d sample of the %dx%d workload" % (n_s, n_s, args.n, args.n),
+                   "m": n_s, "n": n_s, "b": args.b, "q": args.q, "spectrum": args.spectrum},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def measure_fp64_peak(torch, dev) -> float:
+    """cuBLAS DGEMM 8192^3 throughput (TFLOP/s), the FP64 tensor denominator."""
+    n = 8192
+    a = torch.randn(n, n, device=dev, dtype=torch.float64)
+    bm = torch.randn(n, n, device=dev, dtype=torch.float64)
+    c = a @ bm
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c = a @ bm
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, bm, c
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def run_gb300(args, rank: int, world: int, local_rank: int):
+    import torch
+
+    import paper_2104_05782_gb300 as rutv
+    import synthetic
+    from paper_2104_05782_gb300 import build as rbuild
+
+    rbuild.build()
+    rutv.load()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    m = n = args.n
+    b, q = args.b, args.q
+    prec = {"fp64": rutv.RANDUTV_FP64, "bf16": rutv.RANDUTV_SKETCH_BF16}[args.prec]
+    F = randutv_flops(m, n, b, q)
+    A, sigma = synthetic.test_matrix_device(m, n, args.spectrum, 1 + 2 * rank, 2 + 2 * rank, device=dev)
+    torch.cuda.synchronize()
+    fp64_peak = measure_fp64_peak(torch, dev)
+
+    T = rutv.colmajor_empty(m, n, dev)
+    U = rutv.colmajor_empty(m, m, dev)
+    V = rutv.colmajor_empty(n, n, dev)
+    ws_bytes = rutv.randutv_workspace_size(m, n, b, prec)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        st = rutv.randutv_factor_ex(m, n, A, m, b, q, 0, U, T, V, prec, stream, ws, ws_bytes, -1, None)
+        if st != rutv.RANDUTV_OK:
+            raise rutv.RandUTVError(st, "randutv_factor_ex")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
+    sampler.start()
+    rutv.randutv_trace_reset()
+    rutv.randutv_trace_enable(True)
+    launches0 = rutv.randutv_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    launches = rutv.randutv_launch_count() - launches0
+    rutv.randutv_trace_enable(False)
+    trace = rutv.randutv_trace_read()
+    clocks = sampler.stop()
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * F / (ms_per_step * 1e-3) / 1e12
+
+    # quality of this run (not timed): diagonal of T against the prescribed spectrum
+    d = torch.diagonal(T).abs().cpu().numpy()
+    quality = None
+    if sigma is not None:
+        import numpy as np
+        r = d / sigma
+        quality = {"Tii_over_sigma_median": float(np.median(r)), "Tii_over_sigma_first_block_max_dev":
+                   float(np.abs(r[:b] - 1).max())}
+
+    # dominant kernel: the FP64 DMMA GEMM (all its launches, with their split-K reduce)
+    g_ms = sum(v["ms"] for k, v in trace.items() if k.startswith("gemm"))
+    g_fl = sum(v["flops"] for k, v in trace.items() if k.startswith("gemm"))
+    g_launch = sum(v["scopes"] for k, v in trace.items() if k.startswith("gemm"))
+    tot_ms = sum(v["ms"] for v in trace.values())
+    achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None
+    roofline = {
+        "kernel": "k_gemm_f64 (FP64 mma.sync m8n8k4, with its split-K reduce)",
+        "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+        "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+        "peak_source": "cuBLAS DGEMM 8192^3 measured in this run (MEASURED_PEAKS.json has no FP64 entry)",
+        "launches": g_launch, "share_of_traced_time": g_ms / tot_ms if tot_ms else None,
+        "avg_flops_per_launch": g_fl / max(g_launch, 1),
+        "avg_ms_per_launch": g_ms / max(g_launch, 1),
+    }
+    breakdown = {k: {"ms": round(v["ms"] / args.steps, 3), "launches": v["kernels"] // args.steps}
+                 for k, v in sorted(trace.items(), key=lambda kv: -kv[1]["ms"])}
+
+    # end to end through the C ABI on HOST buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        Ah = A.t().contiguous().cpu().pin_memory()   # row-major A^T == column-major A
+        Th = torch.empty((n, m), dtype=torch.float64).pin_memory()
+        Uh = torch.empty((m, m), dtype=torch.float64).pin_memory()
+        Vh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        del T, U, V, ws
+        torch.cuda.empty_cache()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        st = rutv.randutv_factor_host(m, n, Ah, m, b, q, 0, Uh, Th, Vh, prec)
+        t_e2e = time.perf_counter() - t0
+        if st != rutv.RANDUTV_OK:
+            raise rutv.RandUTVError(st, "randutv_factor_host")
+        if dist:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * F / t_e2e / 1e12, "unit": "TFLOP/s", "s_per_factorization": t_e2e,
+               "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * (m * n + m * m + n * n),
+               "api": "randutv_factor_host (pinned host buffers, copies and device allocation inside)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        n_s = 2048
+        val, secs, cores = cpu_oracle_sample(n_s, b, q, args.spectrum)
+        cpu = {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": "one %dx%d %s-spectrum factorization (b=%d, q=%d, U and V formed), %.1f s; "
+                         "TFLOP/s from the same flop formula" % (n_s, n_s, args.spectrum, b, q, secs)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "s_per_factorization": ms_per_step / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.prec == "fp64" else "f64+bf16-sketch", "data": "synthetic",
+            "config": {"workload": "randUTV %s %dx%d, %s spectrum, b=%d, q=%d, U and V formed" %
+                       (args.prec.upper(), m, n, args.spectrum, b, q),
+                       "m": m, "n": n, "b": b, "q": q, "spectrum": args.spectrum, "precision": args.prec,
+                       "flops_per_factorization": F,
+                       "l2": "inputs larger than L2 (A, T, U, V are 2.05 GB each)",
+                       "parallelism": "replicas x%d" % world},
+            "fp64_peak_tflops": fp64_peak,
+            "pct_of_fp64_peak": 100.0 * (value / world) / fp64_peak,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "breakdown_ms_per_step": breakdown,
+            "quality": quality,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--n", type=int, default=16000)
+    p.add_argument("--b", type=int, default=128)
+    p.add_argument("--q", type=int, default=2)
+    p.add_argument("--spectrum", default="gap")
+    p.add_argument("--prec", default="fp64", choices=["fp64", "bf16"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    args = p.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gb300(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,143 @@
+// misc.cu -- element-wise kernels of the randUTV step: the Gaussian draw of the
+// sketch, identity initialisation, strided copies, the diagonal block write and
+// the finiteness check.
+#include "common.cuh"
+#include "internal.h"
+#include "trace.h"
+
+namespace rutv {
+
+namespace {
+
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 64 x 64 -> 128-bit multiplies, key bumped by the Weyl constants.
+__device__ __forceinline__ void philox4x64_10(uint64_t x[4], uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        uint64_t hi0 = __umul64hi(M0, x[0]), lo0 = M0 * x[0];
+        uint64_t hi1 = __umul64hi(M1, x[2]), lo1 = M1 * x[2];
+        uint64_t y0 = hi1 ^ x[1] ^ k0, y2 = hi0 ^ x[3] ^ k1;
+        x[0] = y0; x[1] = lo1; x[2] = y2; x[3] = lo0;
+    }
+}
+
+// G^(step)(r, c), Sec. 3.2.1: counter (r/4, c, step, 0), key (seed, 0); each
+// word -> u = (floor(x/2^11) + 1) 2^-53 in (0,1]; Box-Muller on pairs
+// (u0,u1) -> rows 4k, 4k+1 and (u2,u3) -> rows 4k+2, 4k+3.
+__global__ void k_gaussian(uint64_t seed, int64_t step, int64_t rows, int64_t cols, double* __restrict__ G,
+                           int64_t ldg) {
+    const int64_t groups = (rows + 3) / 4;
+    const int64_t total = groups * cols;
+    const double two_pi = 6.283185307179586476925286766559;
+    const double inv53 = 1.0 / 9007199254740992.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = e % groups, c = e / groups;
+        uint64_t x[4] = {(uint64_t)k, (uint64_t)c, (uint64_t)step, 0};
+        philox4x64_10(x, seed, 0);
+        double z[4];
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr) {
+            double ua = ((double)(x[2 * pr] >> 11) + 1.0) * inv53;
+            double ub = ((double)(x[2 * pr + 1] >> 11) + 1.0) * inv53;
+            double rad = sqrt(-2.0 * log(ua));
+            double s, co;
+            sincos(two_pi * ub, &s, &co);
+            z[2 * pr] = rad * co;
+            z[2 * pr + 1] = rad * s;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            int64_t r = 4 * k + t;
+            if (r < rows) G[r + c * ldg] = z[t];
+        }
+    }
+}
+
+__global__ void k_set_identity(double* __restrict__ X, int64_t n, int64_t ld) {
+    int64_t total = n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e % n, j = e / n;
+        X[i + j * ld] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+__global__ void k_copy(const double* __restrict__ src, int64_t lds, double* __restrict__ dst, int64_t ldd,
+                       int64_t rows, int64_t cols) {
+    int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e % rows, j = e / rows;
+        dst[i + j * ldd] = src[i + j * lds];
+    }
+}
+
+__global__ void k_set_diag_block(double* __restrict__ T, int64_t ldt, int64_t k0, int64_t m, int w,
+                                 const double* __restrict__ D) {
+    int64_t rows = m - k0;
+    int64_t total = rows * w;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e % rows, j = e / rows;
+        T[(k0 + i) + (k0 + j) * ldt] = (i == j) ? D[j] : 0.0;
+    }
+}
+
+__global__ void k_check_finite(const double* __restrict__ X, int64_t ld, int64_t rows, int64_t cols, int* status) {
+    int64_t total = rows * cols;
+    bool bad = false;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e % rows, j = e / rows;
+        bad |= !isfinite(X[i + j * ld]);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
+}
+
+unsigned grid_for(int64_t total) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 8192)); }
+
+}  // namespace
+
+cudaError_t gaussian_f64(uint64_t seed, int64_t step, int64_t rows, int64_t cols, double* G, int64_t ldg,
+                         cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    k_gaussian<<<grid_for(cdiv(rows, 4) * cols), 256, 0, st>>>(seed, step, rows, cols, G, ldg);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t set_identity(double* X, int64_t n, int64_t ld, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_set_identity<<<grid_for(n * n), 256, 0, st>>>(X, n, ld);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t copy_matrix(const double* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int64_t cols,
+                        cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    k_copy<<<grid_for(rows * cols), 256, 0, st>>>(src, lds, dst, ldd, rows, cols);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t set_diag_block(double* T, int64_t ldt, int64_t k0, int64_t m, int w, const double* D,
+                           cudaStream_t st) {
+    if (w <= 0 || m - k0 <= 0) return cudaSuccess;
+    k_set_diag_block<<<grid_for((m - k0) * w), 256, 0, st>>>(T, ldt, k0, m, w, D);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t check_finite(const double* X, int64_t ld, int64_t rows, int64_t cols, int* status, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    k_check_finite<<<grid_for(rows * cols), 256, 0, st>>>(X, ld, rows, cols, status);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+}  // namespace rutv

@@ -1,0 +1,281 @@
+// panel.cu -- Householder QR of a tall panel and the compact-WY triangular factor.
+//
+// The QR of the sketch Y (n' x b, builds V_alpha, Sec. 3.2.1) and the QR of the
+// panel T22(:, 1:b) (m' x b, builds U_alpha, Sec. 3.2.2) are the chains of b
+// dependent reflectors that Sec. 4.1 calls the synchronisation points of the
+// algorithm.  Each reflector follows LAPACK's dlarfg rule (Sec. 2.2 "HQR"):
+//   alpha = P(j,j), x = P(j+1:, j), xi = |x|;  xi == 0 -> tau = 0;
+//   else beta = -sign(alpha) hypot(alpha, xi), tau = (beta - alpha)/beta,
+//        v = x / (alpha - beta), P(j,j) = beta,
+// and H_j = I - tau [1; v][1; v]^T is applied to the columns right of j.
+//
+// GB300 design: one cooperative launch over up to one block per SM.  Block g
+// owns a contiguous slab of rows, so every entry of the panel is read and
+// written by one block only and stays in that SM's L1/L2 path.  Each column
+// needs exactly ONE grid barrier: in the same pass that applies H_j to its
+// rows, a block also forms its partial sums sum_r x_r^2 and sum_r x_r P(r,c)
+// for the NEXT column (x = the next sub-column, c > j+1).  Those partials are
+// all that is needed to build the next reflector and its row vector
+// w_c = P(j,c) + (sum_r x_r P(r,c)) / (alpha - beta), so after the barrier
+// every block reduces them itself, in the same fixed block order (the result
+// is deterministic and identical in every block).  The row j values needed by
+// all blocks travel through a small pivot buffer written by the block owning
+// that row.  Partials and pivot rows are double-buffered by column parity.
+#include "common.cuh"
+#include "internal.h"
+#include "trace.h"
+
+namespace rutv {
+
+namespace {
+
+constexpr int PNT = 256;          // threads per block of the panel kernel
+constexpr int kMaxChunk = 4096;   // rows per block (shared-memory bound)
+
+__global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_t ld, int len, int w,
+                                                  double* __restrict__ tau, double* __restrict__ part,
+                                                  double* __restrict__ piv, unsigned* bar, int* status,
+                                                  int chunk) {
+    extern __shared__ double smem[];
+    double* xsb0 = smem;
+    double* xsb1 = smem + chunk;
+    double* sred = smem + 2 * chunk;
+    double* wv = sred + w;
+    __shared__ double s_scalars[4];
+
+    const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int NW = PNT / 32;
+    const int r0 = cta * chunk;
+    const int r1 = min(len, r0 + chunk);
+    const int nr = max(0, r1 - r0);
+    unsigned target = 0;
+
+    // ---- prologue: partials of column 0 ------------------------------------
+    for (int t = tid; t < nr; t += PNT) {
+        int r = r0 + t;
+        xsb0[t] = (r > 0) ? P[r] : 0.0;
+    }
+    __syncthreads();
+    for (int c = warp; c < w; c += NW) {
+        double acc = 0.0;
+        for (int t = lane; t < nr; t += 32) {
+            double y = (c == 0) ? xsb0[t] : P[(r0 + t) + (int64_t)c * ld];
+            acc += xsb0[t] * y;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) part[(size_t)cta * w + c] = acc;
+    }
+    if (r0 <= 0 && 0 < r1)
+        for (int c = tid; c < w; c += PNT) piv[c] = P[(int64_t)c * ld];
+    if (!grid_sync(bar, target, status)) return;
+
+    for (int j = 0; j < w; ++j) {
+        const int p = j & 1;
+        double* xc = p ? xsb1 : xsb0;
+        double* xn = p ? xsb0 : xsb1;
+        const double* pp = part + (size_t)p * G * w;
+        const double* pv = piv + (size_t)p * w;
+
+        // reduce the partials of columns j..w-1 (fixed block order)
+        for (int c = j + tid; c < w; c += PNT) {
+            double s = 0.0;
+            for (int g = 0; g < G; ++g) s += __ldcg(pp + (size_t)g * w + c);
+            sred[c] = s;
+        }
+        if (tid == 0) {
+            double alpha = __ldcg(pv + j);
+            double xi2 = sred[j];
+            double tj = 0.0, beta = alpha, d = 1.0, act = 0.0;
+            if (!isfinite(xi2) || !isfinite(alpha)) {
+                atomicOr(status, ST_NONFINITE);
+            } else if (xi2 > 0.0) {
+                double h = hypot(alpha, sqrt(xi2));
+                beta = (alpha >= 0.0) ? -h : h;
+                tj = (beta - alpha) / beta;
+                d = alpha - beta;
+                act = 1.0;
+            }
+            s_scalars[0] = tj;
+            s_scalars[1] = beta;
+            s_scalars[2] = d;
+            s_scalars[3] = act;
+            if (cta == 0) tau[j] = tj;
+        }
+        __syncthreads();
+        const double tj = s_scalars[0], beta = s_scalars[1], d = s_scalars[2];
+        const bool act = s_scalars[3] != 0.0;
+        for (int c = j + 1 + tid; c < w; c += PNT) wv[c] = act ? (__ldcg(pv + c) + sred[c] / d) : 0.0;
+
+        // (a) v_r = x_r / d on own rows r > j; P(j,j) = beta
+        if (act) {
+            for (int t = tid; t < nr; t += PNT) {
+                int r = r0 + t;
+                if (r > j) {
+                    double v = xc[t] / d;
+                    xc[t] = v;
+                    P[r + (int64_t)j * ld] = v;
+                }
+            }
+            if (tid == 0 && r0 <= j && j < r1) P[j + (int64_t)j * ld] = beta;
+        }
+        __syncthreads();
+        if (j + 1 >= w) break;
+
+        // (b1) column j+1 on own rows r > j; next sub-column x' (rows > j+1); row j
+        for (int t = tid; t < nr; t += PNT) {
+            int r = r0 + t;
+            double val = 0.0;
+            if (r > j) {
+                double* e = P + r + (int64_t)(j + 1) * ld;
+                val = *e;
+                if (act) {
+                    val -= tj * xc[t] * wv[j + 1];
+                    *e = val;
+                }
+            }
+            xn[t] = (r > j + 1) ? val : 0.0;
+        }
+        if (act && r0 <= j && j < r1)
+            for (int c = j + 1 + tid; c < w; c += PNT) P[j + (int64_t)c * ld] = __ldcg(pv + c) - tj * wv[c];
+        __syncthreads();
+
+        // (b2) columns c >= j+2: apply H_j, accumulate the next column's partials
+        double* pn = part + (size_t)(p ^ 1) * G * w + (size_t)cta * w;
+        for (int c = j + 1 + warp; c < w; c += NW) {
+            double acc = 0.0;
+            if (c == j + 1) {
+                for (int t = lane; t < nr; t += 32) acc += xn[t] * xn[t];
+            } else {
+                const double wc = wv[c];
+                for (int t = lane; t < nr; t += 32) {
+                    int r = r0 + t;
+                    if (r > j) {
+                        double* e = P + r + (int64_t)c * ld;
+                        double val = *e;
+                        if (act) {
+                            val -= tj * xc[t] * wc;
+                            *e = val;
+                        }
+                        acc += xn[t] * val;
+                    }
+                }
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) pn[c] = acc;
+        }
+        __syncthreads();
+        if (r0 <= j + 1 && j + 1 < r1)
+            for (int c = j + 1 + tid; c < w; c += PNT)
+                piv[(size_t)(p ^ 1) * w + c] = P[(j + 1) + (int64_t)c * ld];
+        if (!grid_sync(bar, target, status)) return;
+    }
+}
+
+__global__ void k_extract_w(const double* __restrict__ P, int64_t ld, int len, int w, double* __restrict__ W) {
+    int64_t total = (int64_t)len * w;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int r = (int)(e % len);
+        int c = (int)(e / len);
+        W[e] = (r < c) ? 0.0 : (r == c ? 1.0 : P[r + (int64_t)c * ld]);
+    }
+}
+
+// Forward column-wise recurrence (Sec. 2.3 compact WY):
+//   Tf(j,j) = tau_j,  Tf(0:j, j) = -tau_j Tf(0:j, 0:j) (W^T W)(0:j, j).
+// One block; rows of the triangular mat-vec are spread over warps, the sum
+// over l over lanes.  Ts is a row-major working copy (shared memory when it
+// fits, else the caller's scratch passed as Tf's storage area).
+__global__ void __launch_bounds__(256) k_tfactor(const double* __restrict__ gram, const double* __restrict__ tau,
+                                                 int w, double* __restrict__ Tf, double* __restrict__ gscr,
+                                                 int use_smem, int* status) {
+    extern __shared__ double tsm[];
+    double* Ts = use_smem ? tsm : gscr;  // row-major: Ts[i*w + l]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < w * w; e += blockDim.x) Ts[e] = 0.0;
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+        const double tj = tau[j];
+        for (int i = warp; i < j; i += 8) {
+            double s = 0.0;
+            for (int l = i + lane; l < j; l += 32) s += Ts[(size_t)i * w + l] * gram[l + (size_t)j * w];
+            s = warp_sum(s);
+            if (lane == 0) Ts[(size_t)i * w + j] = -tj * s;
+        }
+        if (tid == 0) {
+            Ts[(size_t)j * w + j] = tj;
+            if (!isfinite(tj)) atomicOr(status, ST_NONFINITE);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < w * w; e += blockDim.x) {
+        int i = e % w, jj = e / w;
+        Tf[e] = Ts[(size_t)i * w + jj];
+    }
+}
+
+}  // namespace
+
+int panel_qr_grid(int64_t len, int w, int sms) {
+    (void)w;
+    int64_t g = cdiv(len, 64);
+    if (g > sms) g = sms;
+    if (g < 1) g = 1;
+    while (cdiv(len, g) > kMaxChunk) ++g;  // only for len > sms * kMaxChunk
+    return (int)g;
+}
+
+size_t panel_qr_scratch_elems(int w, int grid) { return (size_t)2 * grid * w + (size_t)2 * w; }
+
+cudaError_t panel_qr(double* P, int64_t ld, int64_t len, int w, double* tau, double* scratch, unsigned* bar,
+                     int* status, int sms, cudaStream_t st) {
+    if (len <= 0 || w <= 0) return cudaSuccess;
+    int G = panel_qr_grid(len, w, sms);
+    int chunk = (int)cdiv(len, G);
+    if (chunk > kMaxChunk || G > sms) return cudaErrorInvalidValue;
+    double* part = scratch;
+    double* piv = scratch + (size_t)2 * G * w;
+    size_t shm = sizeof(double) * ((size_t)2 * chunk + (size_t)2 * w);
+    static thread_local size_t configured = 0;
+    if (shm > 48 * 1024 && shm > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_panel_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (e != cudaSuccess) return e;
+        configured = shm;
+    }
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    int len_i = (int)len;
+    void* args[] = {&P, &ld, &len_i, &w, &tau, &part, &piv, &bar, &status, &chunk};
+    trace_count(1);
+    return cudaLaunchCooperativeKernel((const void*)k_panel_qr, dim3(G), dim3(PNT), args, shm, st);
+}
+
+cudaError_t extract_w(const double* P, int64_t ld, int64_t len, int w, double* W, cudaStream_t st) {
+    if (len <= 0 || w <= 0) return cudaSuccess;
+    int64_t total = len * w;
+    unsigned blocks = (unsigned)std::min<int64_t>(cdiv(total, 256), 4096);
+    k_extract_w<<<blocks, 256, 0, st>>>(P, ld, (int)len, w, W);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t tfactor(const double* gram, const double* tau, int w, double* Tf, int* status, cudaStream_t st) {
+    if (w <= 0) return cudaSuccess;
+    size_t bytes = sizeof(double) * (size_t)w * w;
+    int use_smem = bytes <= 200 * 1024;
+    // without shared memory the row-major working copy lives behind Tf's
+    // column-major result (the caller reserves 2 w^2 doubles).
+    double* gscr = Tf + (size_t)w * w;
+    size_t shm = use_smem ? bytes : 0;
+    static thread_local size_t configured = 0;
+    if (shm > 48 * 1024 && shm > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_tfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (e != cudaSuccess) return e;
+        configured = shm;
+    }
+    k_tfactor<<<1, 256, shm, st>>>(gram, tau, w, Tf, gscr, use_smem, status);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+}  // namespace rutv

@@ -1,0 +1,170 @@
+"""CUDA path vs the CPU oracle, through the C ABI (needs a GB300).
+
+Entrywise parity on T (|dT| <= 1e-10 ||A||_F), U and V, plus the residual and
+orthogonality bounds 50 n 2^-53 of a UTV factorization (Sec. 3.1), on seeded
+synthetic inputs that span several 64 x 64 tiles, ragged tails, b not dividing
+n, tall m = 2n, b >= n, the T-only mode and early termination.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from conftest import utv_bound
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rutv():
+    import paper_2104_05782_gb300 as r
+    from paper_2104_05782_gb300 import build
+    build.build()
+    r.load()
+    assert torch.cuda.is_available()
+    return r
+
+
+def to_dev(A):
+    return torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+
+
+def to_host(X):
+    return None if X is None else X.t().contiguous().cpu().numpy().T
+
+
+def gpu_factor(rutv, A, b, q, seed, want_uv=True, stop_after=-1, prec=0):
+    U, T, V = rutv.factor(to_dev(A), b, q, seed, want_uv=want_uv, stop_after=stop_after, prec=prec)
+    torch.cuda.synchronize()
+    return to_host(U), to_host(T), to_host(V)
+
+
+def check_parity(A, got, want, tol=1e-10):
+    """|dT| <= tol ||A||_F entrywise; U and V through U T and T V^T.
+
+    A column of U or V that pairs with a singular value sigma_j is determined
+    only to about eps ||A|| / gap_j (gap to the nearest other singular value),
+    e.g. ~1e-5 for sigma ~ 1e-10 spaced 2e-12 apart in the 1000 x 1000
+    geometric spectrum, so U and V are not compared entry by entry.  The
+    products U T = A V and T V^T = U^T A weight each column by its row/column
+    of T and are determined to the same absolute level as T.
+    """
+    Ug, Tg, Vg = got
+    Uo, To, Vo = want
+    nrm = np.linalg.norm(A)
+    dT = np.abs(Tg - To).max()
+    assert dT <= tol * nrm, "max |dT| = %.3e (||A||_F = %.3e)" % (dT, nrm)
+    if Uo is not None:
+        dUT = np.abs(Ug @ Tg - Uo @ To).max()
+        dTV = np.abs(Tg @ Vg.T - To @ Vo.T).max()
+        assert dUT <= tol * nrm, "max |d(UT)| = %.3e" % dUT
+        assert dTV <= tol * nrm, "max |d(TV^T)| = %.3e" % dTV
+
+
+def check_utv(A, U, T, V, triangular=True):
+    m, n = A.shape
+    nrm = np.linalg.norm(A)
+    assert np.linalg.norm(A - U @ T @ V.T) / nrm <= utv_bound(n)
+    assert np.linalg.norm(U.T @ U - np.eye(m)) <= utv_bound(m)
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= utv_bound(n)
+    if triangular:
+        assert np.array_equal(np.tril(T, -1), np.zeros_like(T))
+
+
+@pytest.mark.parametrize("m,n,b,q,kind,seed", [
+    (1000, 1000, 64, 1, "geometric10", 0),   # the 1000^2 parity workload
+    (300, 300, 64, 2, "normal", 3),          # 5 steps + ragged final block of 44
+    (333, 200, 48, 1, "geometric10", 7),     # tall, ragged rows and columns
+    (256, 128, 32, 0, "normal", 1),          # m = 2n, q = 0
+    (130, 130, 200, 1, "normal", 2),         # b >= n: single panel QR + SVD
+    (97, 1, 16, 1, "normal", 5),             # one column
+    (64, 64, 1, 1, "normal", 4),             # b = 1
+    (200, 150, 17, 3, "geometric10", 9),     # odd b (Jacobi padding), q = 3
+])
+def test_parity_against_oracle(rutv, m, n, b, q, kind, seed):
+    A = synthetic.test_matrix(m, n, kind, 10 + seed, 20 + seed)
+    got = gpu_factor(rutv, A, b, q, seed)
+    want = oracle.randutv(A, b, q, seed)[:3]
+    check_parity(A, got, want)
+    check_utv(A, *got)
+
+
+@pytest.mark.parametrize("m,n,b,q", [(256, 128, 32, 0), (400, 400, 64, 2)])
+def test_gap_spectrum_diagonal_and_invariants(rutv, m, n, b, q):
+    """sigma = 1 repeated n/10 times: the singular vectors of a diagonal block
+    are not unique there, so only what is unique is compared entrywise -- the
+    diagonal of T (the trailing matrix never depends on the rotation chosen
+    inside a degenerate block) -- and the rest is checked for validity."""
+    A = synthetic.test_matrix(m, n, "gap", 31, 32)
+    got = gpu_factor(rutv, A, b, q, 3)
+    want = oracle.randutv(A, b, q, 3)[:3]
+    nrm = np.linalg.norm(A)
+    assert np.abs(np.diag(got[1]) - np.diag(want[1])).max() <= 1e-10 * nrm
+    check_utv(A, *got)
+    # row norms of each block row of T are invariant under the block's rotation
+    for k0 in range(0, n, b):
+        rg = np.linalg.norm(got[1][k0:k0 + b, k0:])
+        ro = np.linalg.norm(want[1][k0:k0 + b, k0:])
+        assert abs(rg - ro) <= 1e-10 * nrm
+
+
+def test_parity_t_only_mode(rutv):
+    A = synthetic.test_matrix(400, 300, "geometric10", 1, 2)
+    U, T, V = gpu_factor(rutv, A, 64, 1, 0, want_uv=False)
+    assert U is None and V is None
+    _, To, _, _ = oracle.randutv(A, 64, 1, 0, want_uv=False)
+    assert np.abs(T - To).max() <= 1e-10 * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("stop_after", [1, 3])
+def test_parity_early_termination(rutv, stop_after):
+    A = synthetic.test_matrix(300, 260, "geometric10", 5, 6)
+    got = gpu_factor(rutv, A, 40, 1, 2, stop_after=stop_after)
+    want = oracle.randutv(A, 40, 1, 2, stop_after=stop_after)[:3]
+    check_parity(A, got, want)
+    check_utv(A, *got, triangular=False)
+    assert np.array_equal(np.tril(got[1][:, :40 * stop_after], -1), np.zeros((300, 40 * stop_after)))
+
+
+def test_empty_and_zero_matrices(rutv):
+    U, T, V = gpu_factor(rutv, np.zeros((5, 0)), 4, 1, 0)
+    assert T.shape == (5, 0)
+    assert np.array_equal(U, np.eye(5))
+    A = np.zeros((40, 30))
+    U, T, V = gpu_factor(rutv, A, 8, 1, 0)
+    assert np.array_equal(T, np.zeros_like(T))
+    assert np.linalg.norm(U.T @ U - np.eye(40)) <= utv_bound(40)
+    assert np.linalg.norm(V.T @ V - np.eye(30)) <= utv_bound(30)
+
+
+def test_nonfinite_input_reports_status(rutv):
+    A = synthetic.test_matrix(64, 64, "normal", 1, 2)
+    A[5, 7] = np.nan
+    with pytest.raises(rutv.RandUTVError) as ei:
+        rutv.factor(to_dev(A), 16, 1, 0)
+    assert ei.value.status == rutv.RANDUTV_ENONFINITE
+    # the context stays usable
+    A[5, 7] = 0.0
+    rutv.factor(to_dev(A), 16, 1, 0)
+
+
+def test_deterministic_repeat(rutv):
+    A = synthetic.test_matrix(500, 400, "normal", 3, 4)
+    r1 = gpu_factor(rutv, A, 64, 2, 11)
+    r2 = gpu_factor(rutv, A, 64, 2, 11)
+    for x, y in zip(r1, r2):
+        assert np.array_equal(x, y)
+
+
+def test_host_entry_point_matches_device(rutv):
+    m, n, b, q = 260, 200, 32, 1
+    A = synthetic.test_matrix(m, n, "geometric10", 8, 9)
+    U = np.zeros((m, m), order="F")
+    T = np.zeros((m, n), order="F")
+    V = np.zeros((n, n), order="F")
+    Af = np.asfortranarray(A)
+    assert rutv.randutv_factor_host(m, n, Af, m, b, q, 3, U, T, V) == rutv.RANDUTV_OK
+    got = gpu_factor(rutv, A, b, q, 3)
+    assert np.array_equal(T, got[1]) and np.array_equal(U, got[0]) and np.array_equal(V, got[2])
