@@ -30,6 +30,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "randUTV s/factorization & TFLOP/s at n=16000: mixed/learned-q vs FP64, % peak"
+# ncu: 222.2 MB of DRAM traffic for the 4.295 GFLOP rank-128 update launch (4096^2)
+GEMM_F64_DRAM_BYTES_PER_FLOP = 222.2e6 / (2.0 * 4096 * 4096 * 128)
 
 
 def randutv_flops(m: int, n: int, b: int, q: int, uv: bool = True) -> float:
@@ -205,7 +207,8 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
 
     m = n = args.n
     b, q = args.b, args.q
-    prec = {"fp64": rutv.RANDUTV_FP64, "bf16": rutv.RANDUTV_SKETCH_BF16}[args.prec]
+    prec = {"fp64": rutv.RANDUTV_FP64, "bf16": rutv.RANDUTV_SKETCH_BF16,
+            "fp16": rutv.RANDUTV_SKETCH_FP16_SCALED}[args.prec]
     F = randutv_flops(m, n, b, q)
     A, sigma = synthetic.test_matrix_device(m, n, args.spectrum, 1 + 2 * rank, 2 + 2 * rank, device=dev)
     torch.cuda.synchronize()
@@ -274,7 +277,13 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
     roofline = {
         "kernel": "k_gemm_f64 (FP64 mma.sync m8n8k4, with its split-K reduce)",
         "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-        "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+        "frac": (achieved / fp64_peak) if achieved else None,
+        # DRAM bytes per flop of one ncu-captured launch of this kernel (the
+        # 4096^2 rank-128 update, profiles/gemm_f64_rank128_4096.md) times the
+        # average flops of a launch here
+        "traffic": GEMM_F64_DRAM_BYTES_PER_FLOP * g_fl / max(g_launch, 1),
+        "traffic_source": "ncu dram__bytes_read+write of k_gemm_f64 on the 4096^2 case (0.0518 B/flop), "
+                          "scaled by the average flops per launch",
         "peak_source": "cuBLAS DGEMM 8192^3 measured in this run (MEASURED_PEAKS.json has no FP64 entry)",
         "launches": g_launch, "share_of_traced_time": g_ms / tot_ms if tot_ms else None,
         "avg_flops_per_launch": g_fl / max(g_launch, 1),
@@ -320,7 +329,7 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "s_per_factorization": ms_per_step / 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.prec == "fp64" else "f64+bf16-sketch", "data": "synthetic",
+            "dtype": "f64" if args.prec == "fp64" else "f64+%s-sketch" % args.prec, "data": "synthetic",
             "config": {"workload": "randUTV %s %dx%d, %s spectrum, b=%d, q=%d, U and V formed" %
                        (args.prec.upper(), m, n, args.spectrum, b, q),
                        "m": m, "n": n, "b": b, "q": q, "spectrum": args.spectrum, "precision": args.prec,
@@ -342,6 +351,102 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
         dist.destroy_process_group()
 
 
+def batched_shapes(count: int, seed: int = 0):
+    """4096-matrix workload: n = round(exp(U[ln 32, ln 512])), 25% tall (m = 2n)."""
+    import numpy as np
+    g = np.random.default_rng(seed)
+    n = np.rint(np.exp(g.uniform(np.log(32.0), np.log(512.0), count))).astype(int)
+    tall = g.uniform(size=count) < 0.25
+    m = np.where(tall, 2 * n, n)
+    return [int(x) for x in m], [int(x) for x in n]
+
+
+def run_batched(args, rank: int, world: int, local_rank: int):
+    """One step = one replay of the whole batch (CUDA graph of one persistent launch)."""
+    import torch
+
+    import paper_2104_05782_gb300 as rutv
+    import synthetic
+    from paper_2104_05782_gb300 import build as rbuild
+
+    rbuild.build()
+    rutv.load()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    count, q = args.count, args.q
+    ms, ns = batched_shapes(count)
+    A, T, U, V = [], [], [], []
+    for k in range(count):
+        a, _ = synthetic.test_matrix_device(ms[k], ns[k], "geometric8", 7 * k + 1 + rank * count * 7,
+                                            7 * k + 2 + rank * count * 7, device=dev)
+        A.append(a)
+        T.append(rutv.colmajor_empty(ms[k], ns[k], dev))
+        U.append(rutv.colmajor_empty(ms[k], ms[k], dev))
+        V.append(rutv.colmajor_empty(ns[k], ns[k], dev))
+    seeds = list(range(count))
+    prec = {"fp64": rutv.RANDUTV_FP64, "fp32": rutv.RANDUTV_SKETCH_FP32}[args.prec if args.prec != "bf16" else "fp64"]
+    t0 = time.perf_counter()
+    r, table = rutv.randutv_batched_autotune(ms, ns, A, ms, U, T, V, seeds, q, prec)
+    t_tune = time.perf_counter() - t0
+    if r != 0:
+        raise rutv.RandUTVError(r, "randutv_batched_autotune")
+    plan = rutv.BatchPlan(ms, ns, A, ms, U, T, V, seeds, q, prec, table)
+    b_of = {}
+    for line in table.strip().splitlines():
+        lo, hi, tall, b = map(int, line.split())
+        b_of[(lo, hi, tall)] = b
+    F = 0.0
+    for k in range(count):
+        b = next(bb for (lo, hi, tl), bb in b_of.items() if lo <= ns[k] <= hi and tl == (1 if ms[k] > ns[k] else 0))
+        F += randutv_flops(ms[k], ns[k], b, q)
+    for _ in range(args.warmup):
+        plan.run()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    l0 = rutv.randutv_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    e0.record(stream)
+    worst = 0
+    for _ in range(args.steps):
+        r, st = plan.run()
+        worst = max(worst, r)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    launches = rutv.randutv_launch_count() - l0
+    clocks = sampler.stop()
+    if dist:
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    plan.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": world * F / (ms_step * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "s_per_batch": ms_step / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.prec != "fp32" else "f64+fp32-sketch", "data": "synthetic",
+            "config": {"workload": "batched randUTV, %d matrices, n log-uniform in [32, 512], 25%% with m = 2n, "
+                                   "sigma_i = 10^(-8(i-1)/(n-1)), q=%d, U and V formed" % (count, q),
+                       "count": count, "q": q, "autotune_table": table, "autotune_seconds": t_tune,
+                       "flops_per_batch": F, "parallelism": "replicas x%d" % world},
+            "status_worst": worst, "gpu_launches": launches, "clocks": clocks}), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -352,7 +457,9 @@ def main():
     p.add_argument("--b", type=int, default=128)
     p.add_argument("--q", type=int, default=2)
     p.add_argument("--spectrum", default="gap")
-    p.add_argument("--prec", default="fp64", choices=["fp64", "bf16"])
+    p.add_argument("--prec", default="fp64", choices=["fp64", "bf16", "fp16", "fp32"])
+    p.add_argument("--workload", default="single", choices=["single", "batched"])
+    p.add_argument("--count", type=int, default=4096)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     args = p.parse_args()
@@ -361,6 +468,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batched":
+        run_batched(args, rank, world, local_rank)
     else:
         run_gb300(args, rank, world, local_rank)
 

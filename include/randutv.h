@@ -110,6 +110,112 @@ randutv_status randutv_factor_host(int64_t m, int64_t n, const double* A, int64_
                                    uint64_t seed, double* U, double* T, double* V, int prec);
 
 /*
+ * Batched randUTV: `count` independent factorizations (each as randutv_factor,
+ * FP64, or with RANDUTV_SKETCH_FP32 for an FP32 sketch) in ONE persistent
+ * kernel.  Each CTA of the kernel pops the next matrix from an atomic queue
+ * ordered longest-processing-time first and runs every block step of the
+ * matrix itself.  Per-matrix block sizes come from an autotune table.
+ *   m, n, lda, seed : host arrays of count entries (m[i] >= n[i], m[i] <= 8192).
+ *   A, T            : host arrays of count DEVICE pointers (A[i] with ld lda[i],
+ *                     T[i] m[i] x n[i] with ld m[i]); U, V: host arrays of device pointers
+ *                     (m x m / n x n) or NULL (no orthonormal factors).
+ *   q               : power-iteration count for every matrix.
+ *   prec            : RANDUTV_FP64 or RANDUTV_SKETCH_FP32.
+ *   autotune_table  : text with lines "nmin nmax tall b" (tall: 1 = m > n,
+ *                     0 = square, -1 = any), e.g. the output of
+ *                     randutv_batched_autotune; NULL = built-in table.
+ *                     Block sizes are clamped to [1, 64].
+ *   status          : host array of count statuses (or NULL), filled on return.
+ * randutv_batched builds a plan, runs it once and frees it (synchronous).
+ * A plan keeps the descriptors on the device and holds the launch as a CUDA
+ * graph; randutv_batched_plan_run replays it (synchronous; the matrices the
+ * pointers name are re-factored from A each run).
+ */
+typedef struct randutv_batch_plan randutv_batch_plan;
+
+randutv_status randutv_batched(int count, const int64_t* m, const int64_t* n, const double* const* A,
+                               const int64_t* lda, double* const* U, double* const* T, double* const* V,
+                               const uint64_t* seed, int q, int prec, const char* autotune_table, int* status,
+                               void* stream);
+randutv_status randutv_batched_plan_create(int count, const int64_t* m, const int64_t* n, const double* const* A,
+                                           const int64_t* lda, double* const* U, double* const* T, double* const* V,
+                                           const uint64_t* seed, int q, int prec, const char* autotune_table,
+                                           randutv_batch_plan** plan);
+randutv_status randutv_batched_plan_run(randutv_batch_plan* plan, int* status, void* stream);
+void randutv_batched_plan_destroy(randutv_batch_plan* plan);
+
+/*
+ * randutv_batched_autotune: for each size class (n in [2^k, 2^(k+1)), square
+ * and tall separately) times the batched kernel on up to 608 members of the
+ * class with b = 16, 32 and 64 and writes the fastest as a table (the format
+ * randutv_batched reads) into table_out (host, table_bytes bytes).  Overwrites
+ * T, U, V of the matrices it runs.  Synchronous.
+ */
+randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64_t* n, const double* const* A,
+                                        const int64_t* lda, double* const* U, double* const* T, double* const* V,
+                                        const uint64_t* seed, int q, int prec, char* table_out, size_t table_bytes,
+                                        void* stream);
+
+/*
+ * Learned power-iteration count.  Sec. 3.2.1 uses a fixed q; here, before the
+ * sketch of every block step, a small network (16 -> 64 -> 64 -> 4, GELU,
+ * FP32, softmax over q in {0,1,2,3}) picks q from 16 features: the decay of
+ * the previous block's diagonal and of the Householder R diagonal of the
+ * q = 0 sketch, each as log10(|d_j| / |d_0|) at j = 0, w/8, ..., 7w/8.
+ * The q = 0 product is reused by the chosen iterations.
+ *   model   : HOST array of randutv_learnq_model_floats() floats (layout:
+ *             W1[16][64] b1[64] W2[64][64] b2[64] W3[64][4] b3[4] mu[16] sd[16],
+ *             inputs standardised as (f - mu) / sd), or NULL -> fixed q = 2.
+ *             A non-finite network output also falls back to q = 2.  The
+ *             network predicts a distribution over the smallest adequate q;
+ *             the step runs the smallest q whose cumulative predicted
+ *             probability reaches 0.9.
+ *   q_used  : HOST array of ceil(n / b) ints (or NULL): the q chosen per
+ *             sketch step, -1 for the final block (no sketch).
+ * Other arguments as randutv_factor / randutv_factor_ex.  Synchronises the
+ * stream once per block step to read the choice.
+ */
+int randutv_learnq_model_floats(void);
+randutv_status randutv_factor_learnedq(int64_t m, int64_t n, const double* A, int64_t lda, int b,
+                                       const float* model, uint64_t seed, double* U, double* T, double* V,
+                                       int* q_used);
+randutv_status randutv_factor_learnedq_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
+                                          const float* model, uint64_t seed, double* U, double* T, double* V,
+                                          int* q_used, int prec, void* stream);
+
+/*
+ * Training data for the network, generated by the method itself: factors A
+ * (device, T device m x n, U and V not formed) along the q = 2 trajectory and,
+ * for each sketch step (up to max_blocks), writes the 16 features (HOST
+ * float[16] each), the label (HOST int: the smallest q in {0,1,2} whose
+ * diagonal sigma(T22 Q1(q)) stays within 5% of the q = 2 one, entry by entry),
+ * and optionally the four candidate diagonals (HOST double[4 * b] each).
+ * *nblocks receives the number of steps written.
+ */
+randutv_status randutv_learnq_trace(int64_t m, int64_t n, const double* A, int64_t lda, int b, uint64_t seed,
+                                    double* T, float* features, int* labels, double* candidates,
+                                    int64_t max_blocks, int64_t* nblocks);
+
+/*
+ * Network training and evaluation on the GPU with the library's own kernels
+ * (all host arrays; the library allocates and frees its device copies):
+ *   randutv_learnq_train   : `epochs` full-batch Adam steps (lr, weight decay
+ *                            wd) on the mean cross-entropy of X (N x 16,
+ *                            row-major) against labels y; model in/out;
+ *                            loss_history (epochs floats) or NULL.
+ *   randutv_learnq_grad    : gradient of that loss at `model` (grad has the
+ *                            model's length; mu and sd entries are left 0)
+ *                            and the loss itself.
+ *   randutv_learnq_predict : softmax probabilities (N x 4) of the network.
+ */
+randutv_status randutv_learnq_train(const float* X, const int* y, int N, int epochs, float lr, float wd,
+                                    float* model, float* loss_history);
+randutv_status randutv_learnq_grad(const float* X, const int* y, int N, const float* model, float* grad,
+                                   float* loss);
+randutv_status randutv_learnq_predict(const float* model, const float* X, int N, float* probs);
+
+
+/*
  * Tracing (the per-task time breakdown of Sec. 5.4 / Sec. 6.1, done with CUDA
  * events).  While enabled, every launcher of the library brackets its kernel
  * launches with a pair of CUDA events on its stream and records the
@@ -122,7 +228,7 @@ randutv_status randutv_factor_host(int64_t m, int64_t n, const double* A, int64_
  *   randutv_trace_reset()     : drops all records.
  *   randutv_launch_count()    : kernels launched by this library since load.
  */
-typedef struct {
+typedef struct randutv_trace_class {
     char name[32];      /* kernel class, e.g. "gemm_right" */
     int64_t scopes;     /* launcher calls */
     int64_t kernels;    /* kernel launches inside them */

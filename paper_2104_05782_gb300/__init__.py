@@ -74,6 +74,42 @@ def load():
     lib.randutv_trace_reset.restype = None
     lib.randutv_launch_count.argtypes = []
     lib.randutv_launch_count.restype = ctypes.c_longlong
+    pa = ctypes.POINTER(ctypes.c_int64)
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    lib.randutv_batched.argtypes = [ctypes.c_int, pa, pa, pp, pa, pp, pp, pp, ctypes.POINTER(ctypes.c_uint64),
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), _vp]
+    lib.randutv_batched.restype = ctypes.c_int
+    lib.randutv_batched_plan_create.argtypes = [ctypes.c_int, pa, pa, pp, pa, pp, pp, pp,
+                                                ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+    lib.randutv_batched_plan_create.restype = ctypes.c_int
+    lib.randutv_batched_plan_run.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), _vp]
+    lib.randutv_batched_plan_run.restype = ctypes.c_int
+    lib.randutv_batched_plan_destroy.argtypes = [_vp]
+    lib.randutv_batched_plan_destroy.restype = None
+    lib.randutv_batched_autotune.argtypes = [ctypes.c_int, pa, pa, pp, pa, pp, pp, pp,
+                                             ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_char_p, ctypes.c_size_t, _vp]
+    lib.randutv_batched_autotune.restype = ctypes.c_int
+    fp = ctypes.POINTER(ctypes.c_float)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.randutv_learnq_model_floats.argtypes = []
+    lib.randutv_learnq_model_floats.restype = ctypes.c_int
+    lib.randutv_factor_learnedq.argtypes = [_i64, _i64, _vp, _i64, ctypes.c_int, fp, ctypes.c_uint64, _vp, _vp, _vp,
+                                            ip]
+    lib.randutv_factor_learnedq.restype = ctypes.c_int
+    lib.randutv_factor_learnedq_ex.argtypes = [_i64, _i64, _vp, _i64, ctypes.c_int, fp, ctypes.c_uint64, _vp, _vp,
+                                               _vp, ip, ctypes.c_int, _vp]
+    lib.randutv_factor_learnedq_ex.restype = ctypes.c_int
+    lib.randutv_learnq_trace.argtypes = [_i64, _i64, _vp, _i64, ctypes.c_int, ctypes.c_uint64, _vp, fp, ip,
+                                         ctypes.POINTER(ctypes.c_double), _i64, ctypes.POINTER(ctypes.c_int64)]
+    lib.randutv_learnq_trace.restype = ctypes.c_int
+    lib.randutv_learnq_train.argtypes = [fp, ip, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float, fp, fp]
+    lib.randutv_learnq_train.restype = ctypes.c_int
+    lib.randutv_learnq_grad.argtypes = [fp, ip, ctypes.c_int, fp, fp, fp]
+    lib.randutv_learnq_grad.restype = ctypes.c_int
+    lib.randutv_learnq_predict.argtypes = [fp, fp, ctypes.c_int, fp]
+    lib.randutv_learnq_predict.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -147,6 +183,155 @@ def randutv_trace_read(max_classes: int = 64) -> dict:
     return out
 
 
+def _batch_arrays(m, n, A, lda, U, T, V, seed):
+    count = len(m)
+    i64 = lambda xs: (ctypes.c_int64 * count)(*[int(x) for x in xs])
+    ptrs = lambda xs: None if xs is None else (ctypes.c_void_p * count)(*[_ptr(x) for x in xs])
+    seeds = (ctypes.c_uint64 * count)(*[int(x) for x in (seed if seed is not None else [0] * count)])
+    return count, i64(m), i64(n), ptrs(A), i64(lda), ptrs(U), ptrs(T), ptrs(V), seeds
+
+
+def randutv_batched(m, n, A, lda, U, T, V, seed, q, prec=RANDUTV_FP64, autotune_table=None, status=None,
+                    stream=None) -> int:
+    """randutv_batched of the C ABI; per-matrix lists of sizes and device buffers."""
+    count, cm, cn, cA, cl, cU, cT, cV, cs = _batch_arrays(m, n, A, lda, U, T, V, seed)
+    st = (ctypes.c_int * count)() if status is not None else None
+    tab = autotune_table.encode() if isinstance(autotune_table, str) else autotune_table
+    r = load().randutv_batched(count, cm, cn, cA, cl, cU, cT, cV, cs, q, prec, tab, st, _stream_handle(stream))
+    if status is not None:
+        status[:] = list(st)
+    return r
+
+
+def randutv_batched_autotune(m, n, A, lda, U, T, V, seed, q, prec=RANDUTV_FP64, stream=None):
+    """randutv_batched_autotune of the C ABI -> (status, table text)."""
+    count, cm, cn, cA, cl, cU, cT, cV, cs = _batch_arrays(m, n, A, lda, U, T, V, seed)
+    buf = ctypes.create_string_buffer(8192)
+    r = load().randutv_batched_autotune(count, cm, cn, cA, cl, cU, cT, cV, cs, q, prec, buf, 8192,
+                                        _stream_handle(stream))
+    return r, buf.value.decode()
+
+
+class BatchPlan:
+    """randutv_batched_plan_create / _run / _destroy: a batch held on the device as a CUDA graph."""
+
+    def __init__(self, m, n, A, lda, U, T, V, seed, q, prec=RANDUTV_FP64, autotune_table=None):
+        count, cm, cn, cA, cl, cU, cT, cV, cs = _batch_arrays(m, n, A, lda, U, T, V, seed)
+        self.count = count
+        self._keep = (A, U, T, V)
+        tab = autotune_table.encode() if isinstance(autotune_table, str) else autotune_table
+        h = ctypes.c_void_p()
+        r = load().randutv_batched_plan_create(count, cm, cn, cA, cl, cU, cT, cV, cs, q, prec, tab, ctypes.byref(h))
+        if r != RANDUTV_OK:
+            raise RandUTVError(r, "randutv_batched_plan_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        """Replay the batch; returns (worst status, per-matrix statuses)."""
+        st = (ctypes.c_int * self.count)()
+        r = load().randutv_batched_plan_run(self.handle, st, _stream_handle(stream))
+        return r, list(st)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().randutv_batched_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- learned q
+def _f32(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _i32(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def randutv_learnq_model_floats() -> int:
+    return int(load().randutv_learnq_model_floats())
+
+
+def randutv_factor_learnedq(m, n, A, lda, b, model, seed, U, T, V, q_used=None, prec=RANDUTV_FP64, stream=None):
+    """randutv_factor_learnedq_ex of the C ABI; model: float32 array or None; returns (status, q_used list)."""
+    import numpy as np
+    nb = -(-n // b) if n > 0 else 0
+    qu, qp = _i32(np.zeros(max(nb, 1), dtype=np.int32))
+    mp = None
+    if model is not None:
+        mk, mp = _f32(model)
+    r = load().randutv_factor_learnedq_ex(m, n, _ptr(A), lda, b, mp, seed, _ptr(U), _ptr(T), _ptr(V), qp, prec,
+                                          _stream_handle(stream))
+    return r, list(qu[:nb])
+
+
+def randutv_learnq_trace(m, n, A, lda, b, seed, T, max_blocks=None, candidates=False):
+    """randutv_learnq_trace of the C ABI -> (status, features (k x 16), labels (k,), candidates (k x 4 x b) or None)."""
+    import numpy as np
+    mb = max_blocks if max_blocks is not None else max(-(-n // b), 1)
+    f, fp = _f32(np.zeros((mb, 16), dtype=np.float32))
+    y, yp = _i32(np.zeros(mb, dtype=np.int32))
+    cand = np.zeros((mb, 4, b), dtype=np.float64) if candidates else None
+    cp = cand.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if candidates else None
+    cnt = ctypes.c_int64(0)
+    r = load().randutv_learnq_trace(m, n, _ptr(A), lda, b, seed, _ptr(T), fp, yp, cp, mb, ctypes.byref(cnt))
+    k = cnt.value
+    return r, f[:k].copy(), y[:k].copy(), (cand[:k].copy() if candidates else None)
+
+
+def randutv_learnq_train(X, y, model, epochs, lr=1e-3, wd=0.0):
+    """randutv_learnq_train of the C ABI -> (status, trained model, loss history)."""
+    import numpy as np
+    X, xp = _f32(X)
+    y, yp = _i32(y)
+    mk, mp = _f32(np.array(model, dtype=np.float32))
+    hist, hp = _f32(np.zeros(max(epochs, 1), dtype=np.float32))
+    r = load().randutv_learnq_train(xp, yp, len(y), epochs, lr, wd, mp, hp)
+    return r, mk, hist[:epochs]
+
+
+def randutv_learnq_grad(X, y, model):
+    """randutv_learnq_grad of the C ABI -> (status, gradient, loss)."""
+    import numpy as np
+    X, xp = _f32(X)
+    y, yp = _i32(y)
+    mk, mp = _f32(model)
+    g, gp = _f32(np.zeros(len(mk), dtype=np.float32))
+    loss = ctypes.c_float(0.0)
+    r = load().randutv_learnq_grad(xp, yp, len(y), mp, gp, ctypes.byref(loss))
+    return r, g, float(loss.value)
+
+
+def randutv_learnq_predict(model, X):
+    """randutv_learnq_predict of the C ABI -> (status, probabilities N x 4)."""
+    import numpy as np
+    X, xp = _f32(X)
+    mk, mp = _f32(model)
+    pr, pp = _f32(np.zeros((X.shape[0], 4), dtype=np.float32))
+    r = load().randutv_learnq_predict(mp, xp, X.shape[0], pp)
+    return r, pr
+
+
+QNET_PATH = os.path.join(_HERE, "qnet.f32")
+
+
+def load_qnet(path: str = QNET_PATH):
+    """Trained learned-q network (float32 parameters) shipped with the package, or None."""
+    import numpy as np
+    if not os.path.exists(path):
+        return None
+    return np.fromfile(path, dtype=np.float32)
+
+
 # ---------------------------------------------------------------- conveniences
 def colmajor_empty(rows, cols, device="cuda"):
     """Uninitialised FP64 column-major (rows x cols) CUDA tensor (a transposed view)."""
@@ -157,6 +342,8 @@ def colmajor_empty(rows, cols, device="cuda"):
 
 def is_colmajor(x) -> bool:
     rows, cols = x.shape
+    if x.numel() == 0:
+        return True
     return x.stride(0) == 1 and (x.stride(1) == rows or cols <= 1) or (rows <= 1 and x.stride(1) >= 1)
 
 

@@ -53,4 +53,33 @@ cudaError_t set_diag_block(double* T, int64_t ldt, int64_t k0, int64_t m, int w,
 cudaError_t check_finite(const double* X, int64_t ld, int64_t rows, int64_t cols, int* status,
                          cudaStream_t st);
 
+// ---- low-precision sketch (tc_gemm.cu, sketch_lowp.cu) ------------------------
+int tc_gemm_npad(int Nb);
+int tc_gemm_splits(int64_t M, int64_t K, int sms);
+cudaError_t tc_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t M, int Nb, int64_t K, bool f16,
+                    float* C, int64_t ldc, int64_t split_stride, int splits, int* status, cudaStream_t st);
+cudaError_t absmax_f64(const double* X, int64_t ld, int64_t rows, int64_t cols, unsigned long long* out,
+                       cudaStream_t st);
+cudaError_t shadow16(const double* T22, int64_t ldt, int64_t rows, int64_t cols, uint16_t* S, int64_t lds,
+                     uint16_t* St, int64_t ldst, bool f16, const unsigned long long* amax, cudaStream_t st);
+cudaError_t pack16_f64(const double* X, int64_t ldx, int64_t L, int b, uint16_t* Xb, int64_t ldb, bool f16,
+                       cudaStream_t st);
+cudaError_t reduce_splits(const float* P, int64_t stride, int splits, int64_t L, int b, int64_t ldp, float* X,
+                          cudaStream_t st);
+cudaError_t f32_to_f64(const float* X, int64_t total, double* Y, cudaStream_t st);
+size_t cholqr_scratch_floats(int b, int sms);
+cudaError_t cholqr32(float* X, int64_t L, int b, int passes, uint16_t* Xb, int64_t ldb, bool f16, float* scratch,
+                     int sms, cudaStream_t st);
+
+// ---- learned q (learnq.cu) --------------------------------------------------
+int learnq_nparam();
+cudaError_t learnq_features(const double* T, int64_t ldt, int64_t k0, int wprev, const double* R, int64_t ldr, int w,
+                            float* f, cudaStream_t st);
+cudaError_t learnq_infer(const float* P, const float* f, int fallback, int* q, cudaStream_t st);
+size_t learnq_train_scratch_floats(int N);
+cudaError_t learnq_train_step(float* P, const float* X, const int* y, int N, float* scratch, float* grads_out,
+                              float* loss_out, int t, float lr, float wd, cudaStream_t st);
+cudaError_t learnq_predict(const float* P, const float* X, int N, float* probs, cudaStream_t st);
+cudaError_t set_eye_rect(double* X, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st);
+
 }  // namespace rutv

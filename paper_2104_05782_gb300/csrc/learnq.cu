@@ -1,0 +1,276 @@
+// learnq.cu -- the learned choice of the power-iteration count q (Sec. 3.2.1
+// fixes q by hand; here a small network picks it per block step).
+//
+// Network: 16 features -> 64 -> 64 -> 4 logits, GELU after both hidden layers,
+// softmax over q in {0, 1, 2, 3}; FP32.  Inputs are standardised with the
+// (mu, sd) stored in the model.  Parameter layout (row-major, x W):
+//   W1[16][64] b1[64] W2[64][64] b2[64] W3[64][4] b3[4] mu[16] sd[16]
+// Features of block step i (written by k_learnq_features):
+//   f[0..7]  = log10(|T_jj| / |T_00|) of the previous diagonal block at
+//              j = 0, w/8, ..., 7w/8 (block 0: copies of f[8..15]);
+//   f[8..15] = log10(|R_jj| / |R_00|) of the Householder R of the q = 0
+//              sketch Y0 = T22^T G at the same j.
+// Training kernels: per-sample forward, per-sample backward, gradient
+// reductions over the batch in a fixed order (deterministic, no atomics),
+// and Adam.  Cross-entropy loss averaged over the batch.
+#include "common.cuh"
+#include "internal.h"
+#include "trace.h"
+
+namespace rutv {
+
+namespace {
+
+constexpr int NI = 16, NH = 64, NO = 4;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NI * NH, OFF_W2 = OFF_B1 + NH, OFF_B2 = OFF_W2 + NH * NH,
+              OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NH * NO, OFF_MU = OFF_B3 + NO, OFF_SD = OFF_MU + NI,
+              NPARAM = OFF_SD + NI;
+constexpr int NTRAIN = OFF_MU;  // trainable parameters (mu, sd are fixed)
+constexpr float kLearnqConfidence = 0.9f;
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float x) {
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// forward of one sample; activations optional
+__device__ void mlp_forward(const float* P, const float* xin, float* pre1, float* h1, float* pre2, float* h2,
+                            float* logits) {
+    float x[NI];
+    for (int i = 0; i < NI; ++i) {
+        float sd = P[OFF_SD + i];
+        x[i] = (xin[i] - P[OFF_MU + i]) / (sd > 0.f ? sd : 1.f);
+    }
+    for (int j = 0; j < NH; ++j) {
+        float s = P[OFF_B1 + j];
+        for (int i = 0; i < NI; ++i) s = fmaf(x[i], P[OFF_W1 + i * NH + j], s);
+        pre1[j] = s;
+        h1[j] = gelu(s);
+    }
+    for (int j = 0; j < NH; ++j) {
+        float s = P[OFF_B2 + j];
+        for (int i = 0; i < NH; ++i) s = fmaf(h1[i], P[OFF_W2 + i * NH + j], s);
+        pre2[j] = s;
+        h2[j] = gelu(s);
+    }
+    for (int k = 0; k < NO; ++k) {
+        float s = P[OFF_B3 + k];
+        for (int i = 0; i < NH; ++i) s = fmaf(h2[i], P[OFF_W3 + i * NO + k], s);
+        logits[k] = s;
+    }
+}
+
+// Features of block step k0 (see the file comment).  R_jj are read from the
+// QR storage of Y0 (ld ldr); the previous block from T.
+__global__ void k_learnq_features(const double* __restrict__ T, int64_t ldt, int64_t k0, int wprev,
+                                  const double* __restrict__ R, int64_t ldr, int w, float* __restrict__ f) {
+    const int t = threadIdx.x;
+    if (t < 8) {
+        int j = (t * w) / 8;
+        double r0 = fabs(R[0]), rj = fabs(R[j + (int64_t)j * ldr]);
+        float v = (r0 > 0.0 && rj > 0.0) ? (float)log10(rj / r0) : -16.0f;
+        f[8 + t] = fmaxf(v, -16.0f);
+    }
+    __syncthreads();
+    if (t < 8) {
+        if (k0 == 0 || wprev <= 0) {
+            f[t] = f[8 + t];
+        } else {
+            int64_t p0 = k0 - wprev;
+            int j = (t * wprev) / 8;
+            double d0 = fabs(T[p0 + p0 * ldt]), dj = fabs(T[(p0 + j) + (p0 + j) * ldt]);
+            float v = (d0 > 0.0 && dj > 0.0) ? (float)log10(dj / d0) : -16.0f;
+            f[t] = fmaxf(v, -16.0f);
+        }
+    }
+}
+
+// The network predicts a distribution over the smallest adequate q.  The
+// choice is risk-controlled: the smallest q whose cumulative predicted
+// probability P(q_min <= q) reaches `confidence` (a plain argmax would accept
+// every block the network is unsure about).  No model or a non-finite output
+// gives `fallback`.
+__global__ void k_learnq_infer(const float* __restrict__ P, const float* __restrict__ f, int fallback,
+                               float confidence, int* q) {
+    if (threadIdx.x != 0) return;
+    if (P == nullptr) {
+        *q = fallback;
+        return;
+    }
+    float pre1[NH], h1[NH], pre2[NH], h2[NH], lg[NO];
+    mlp_forward(P, f, pre1, h1, pre2, h2, lg);
+    bool finite = true;
+    for (int k = 0; k < NO; ++k) finite &= isfinite(lg[k]);
+    if (!finite) {
+        *q = fallback;
+        return;
+    }
+    float mx = lg[0];
+    for (int k = 1; k < NO; ++k) mx = fmaxf(mx, lg[k]);
+    float pk[NO], se = 0.f;
+    for (int k = 0; k < NO; ++k) {
+        pk[k] = expf(lg[k] - mx);
+        se += pk[k];
+    }
+    float cum = 0.f;
+    int choice = NO - 1;
+    for (int k = 0; k < NO; ++k) {
+        cum += pk[k] / se;
+        if (cum >= confidence) {
+            choice = k;
+            break;
+        }
+    }
+    *q = choice;
+}
+
+// per-sample forward + backward of the mean cross-entropy; writes the
+// per-sample pieces the gradient reductions need.
+__global__ void k_mlp_sample(const float* __restrict__ P, const float* __restrict__ X, const int* __restrict__ y,
+                             int N, float* __restrict__ xs, float* __restrict__ h1s, float* __restrict__ h2s,
+                             float* __restrict__ d1s, float* __restrict__ d2s, float* __restrict__ d3s,
+                             float* __restrict__ loss, float* __restrict__ probs) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float pre1[NH], h1[NH], pre2[NH], h2[NH], lg[NO];
+    const float* xin = X + (size_t)n * NI;
+    mlp_forward(P, xin, pre1, h1, pre2, h2, lg);
+    float mx = lg[0];
+    for (int k = 1; k < NO; ++k) mx = fmaxf(mx, lg[k]);
+    float pk[NO], se = 0.f;
+    for (int k = 0; k < NO; ++k) {
+        pk[k] = expf(lg[k] - mx);
+        se += pk[k];
+    }
+    for (int k = 0; k < NO; ++k) pk[k] /= se;
+    const int lab = y ? y[n] : 0;
+    if (loss) loss[n] = -(lg[lab] - mx - logf(se));
+    if (probs)
+        for (int k = 0; k < NO; ++k) probs[(size_t)n * NO + k] = pk[k];
+    if (!xs) return;
+    const float invN = 1.0f / (float)N;
+    float d3[NO];
+    for (int k = 0; k < NO; ++k) d3[k] = (pk[k] - (k == lab ? 1.f : 0.f)) * invN;
+    float d2[NH];
+    for (int j = 0; j < NH; ++j) {
+        float s = 0.f;
+        for (int k = 0; k < NO; ++k) s = fmaf(d3[k], P[OFF_W3 + j * NO + k], s);
+        d2[j] = s * gelu_d(pre2[j]);
+    }
+    float d1[NH];
+    for (int j = 0; j < NH; ++j) {
+        float s = 0.f;
+        for (int k = 0; k < NH; ++k) s = fmaf(d2[k], P[OFF_W2 + j * NH + k], s);
+        d1[j] = s * gelu_d(pre1[j]);
+    }
+    for (int i = 0; i < NI; ++i) {
+        float sd = P[OFF_SD + i];
+        xs[(size_t)n * NI + i] = (xin[i] - P[OFF_MU + i]) / (sd > 0.f ? sd : 1.f);
+    }
+    for (int j = 0; j < NH; ++j) {
+        h1s[(size_t)n * NH + j] = h1[j];
+        h2s[(size_t)n * NH + j] = h2[j];
+        d1s[(size_t)n * NH + j] = d1[j];
+        d2s[(size_t)n * NH + j] = d2[j];
+    }
+    for (int k = 0; k < NO; ++k) d3s[(size_t)n * NO + k] = d3[k];
+}
+
+// gradient entry g (of NTRAIN) = sum over samples in a fixed order
+__global__ void k_mlp_grad(int N, const float* __restrict__ xs, const float* __restrict__ h1s,
+                           const float* __restrict__ h2s, const float* __restrict__ d1s, const float* __restrict__ d2s,
+                           const float* __restrict__ d3s, float* __restrict__ G) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= NTRAIN) return;
+    const float *a = nullptr, *d = nullptr;
+    int na = 0, nd = 0, ia = 0, id = 0;
+    if (g < OFF_B1) { int e = g - OFF_W1; a = xs; na = NI; ia = e / NH; d = d1s; nd = NH; id = e % NH; }
+    else if (g < OFF_W2) { d = d1s; nd = NH; id = g - OFF_B1; }
+    else if (g < OFF_B2) { int e = g - OFF_W2; a = h1s; na = NH; ia = e / NH; d = d2s; nd = NH; id = e % NH; }
+    else if (g < OFF_W3) { d = d2s; nd = NH; id = g - OFF_B2; }
+    else if (g < OFF_B3) { int e = g - OFF_W3; a = h2s; na = NH; ia = e / NO; d = d3s; nd = NO; id = e % NO; }
+    else { d = d3s; nd = NO; id = g - OFF_B3; }
+    float s = 0.f;
+    for (int n = 0; n < N; ++n) {
+        float dv = d[(size_t)n * nd + id];
+        s = fmaf(a ? a[(size_t)n * na + ia] : 1.0f, dv, s);
+    }
+    G[g] = s;
+}
+
+__global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m1,
+                       float* __restrict__ m2, int t, float lr, float wd) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= NTRAIN) return;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    float gr = G[g] + wd * P[g];
+    m1[g] = b1 * m1[g] + (1.f - b1) * gr;
+    m2[g] = b2 * m2[g] + (1.f - b2) * gr * gr;
+    float mh = m1[g] / (1.f - powf(b1, (float)t));
+    float vh = m2[g] / (1.f - powf(b2, (float)t));
+    P[g] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+__global__ void k_sum_loss(const float* __restrict__ l, int N, float* out) {
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int n = 0; n < N; ++n) s += l[n];
+    *out = (float)(s / (N > 0 ? N : 1));
+}
+
+}  // namespace
+
+int learnq_nparam() { return NPARAM; }
+
+cudaError_t learnq_features(const double* T, int64_t ldt, int64_t k0, int wprev, const double* R, int64_t ldr, int w,
+                            float* f, cudaStream_t st) {
+    k_learnq_features<<<1, 32, 0, st>>>(T, ldt, k0, wprev, R, ldr, w, f);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t learnq_infer(const float* P, const float* f, int fallback, int* q, cudaStream_t st) {
+    k_learnq_infer<<<1, 32, 0, st>>>(P, f, fallback, kLearnqConfidence, q);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+size_t learnq_train_scratch_floats(int N) { return (size_t)N * (NI + 4 * NH + NO + 1 + NO) + 4 * NPARAM + 8; }
+
+// One step of (forward, backward[, Adam]) over the batch X (N x 16), labels y.
+// grads: if non-null receives the gradient (NTRAIN floats); t > 0 applies Adam.
+cudaError_t learnq_train_step(float* P, const float* X, const int* y, int N, float* scratch, float* grads_out,
+                              float* loss_out, int t, float lr, float wd, cudaStream_t st) {
+    float* xs = scratch;
+    float* h1s = xs + (size_t)N * NI;
+    float* h2s = h1s + (size_t)N * NH;
+    float* d1s = h2s + (size_t)N * NH;
+    float* d2s = d1s + (size_t)N * NH;
+    float* d3s = d2s + (size_t)N * NH;
+    float* loss = d3s + (size_t)N * NO;
+    float* probs = loss + N;
+    float* G = probs + (size_t)N * NO;
+    float* m1 = G + NPARAM;
+    float* m2 = m1 + NPARAM;
+    k_mlp_sample<<<(N + 127) / 128, 128, 0, st>>>(P, X, y, N, xs, h1s, h2s, d1s, d2s, d3s, loss, nullptr);
+    k_mlp_grad<<<(NTRAIN + 127) / 128, 128, 0, st>>>(N, xs, h1s, h2s, d1s, d2s, d3s, grads_out ? grads_out : G);
+    trace_count(2);
+    if (loss_out) {
+        k_sum_loss<<<1, 32, 0, st>>>(loss, N, loss_out);
+        trace_count(1);
+    }
+    if (t > 0) {
+        k_adam<<<(NTRAIN + 127) / 128, 128, 0, st>>>(P, grads_out ? grads_out : G, m1, m2, t, lr, wd);
+        trace_count(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t learnq_predict(const float* P, const float* X, int N, float* probs, cudaStream_t st) {
+    k_mlp_sample<<<(N + 127) / 128, 128, 0, st>>>(P, X, nullptr, N, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                    nullptr, nullptr, probs);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+}  // namespace rutv

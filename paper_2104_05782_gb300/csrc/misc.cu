@@ -4,51 +4,22 @@
 #include "common.cuh"
 #include "internal.h"
 #include "trace.h"
+#include "philox.cuh"
 
 namespace rutv {
 
 namespace {
 
-// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
-// 64 x 64 -> 128-bit multiplies, key bumped by the Weyl constants.
-__device__ __forceinline__ void philox4x64_10(uint64_t x[4], uint64_t k0, uint64_t k1) {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        if (round > 0) { k0 += W0; k1 += W1; }
-        uint64_t hi0 = __umul64hi(M0, x[0]), lo0 = M0 * x[0];
-        uint64_t hi1 = __umul64hi(M1, x[2]), lo1 = M1 * x[2];
-        uint64_t y0 = hi1 ^ x[1] ^ k0, y2 = hi0 ^ x[3] ^ k1;
-        x[0] = y0; x[1] = lo1; x[2] = y2; x[3] = lo0;
-    }
-}
-
-// G^(step)(r, c), Sec. 3.2.1: counter (r/4, c, step, 0), key (seed, 0); each
-// word -> u = (floor(x/2^11) + 1) 2^-53 in (0,1]; Box-Muller on pairs
-// (u0,u1) -> rows 4k, 4k+1 and (u2,u3) -> rows 4k+2, 4k+3.
+// G^(step)(r, c) of Sec. 3.2.1 (see gaussian4).
 __global__ void k_gaussian(uint64_t seed, int64_t step, int64_t rows, int64_t cols, double* __restrict__ G,
                            int64_t ldg) {
     const int64_t groups = (rows + 3) / 4;
     const int64_t total = groups * cols;
-    const double two_pi = 6.283185307179586476925286766559;
-    const double inv53 = 1.0 / 9007199254740992.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         int64_t k = e % groups, c = e / groups;
-        uint64_t x[4] = {(uint64_t)k, (uint64_t)c, (uint64_t)step, 0};
-        philox4x64_10(x, seed, 0);
         double z[4];
-#pragma unroll
-        for (int pr = 0; pr < 2; ++pr) {
-            double ua = ((double)(x[2 * pr] >> 11) + 1.0) * inv53;
-            double ub = ((double)(x[2 * pr + 1] >> 11) + 1.0) * inv53;
-            double rad = sqrt(-2.0 * log(ua));
-            double s, co;
-            sincos(two_pi * ub, &s, &co);
-            z[2 * pr] = rad * co;
-            z[2 * pr + 1] = rad * s;
-        }
+        gaussian4(seed, step, k, c, z);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             int64_t r = 4 * k + t;
@@ -62,6 +33,15 @@ __global__ void k_set_identity(double* __restrict__ X, int64_t n, int64_t ld) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = e % n, j = e / n;
+        X[i + j * ld] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+__global__ void k_set_eye_rect(double* __restrict__ X, int64_t rows, int64_t cols, int64_t ld) {
+    int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e % rows, j = e / rows;
         X[i + j * ld] = (i == j) ? 1.0 : 0.0;
     }
 }
@@ -113,6 +93,13 @@ cudaError_t gaussian_f64(uint64_t seed, int64_t step, int64_t rows, int64_t cols
 cudaError_t set_identity(double* X, int64_t n, int64_t ld, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     k_set_identity<<<grid_for(n * n), 256, 0, st>>>(X, n, ld);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t set_eye_rect(double* X, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    k_set_eye_rect<<<grid_for(rows * cols), 256, 0, st>>>(X, rows, cols, ld);
     trace_count(1);
     return cudaGetLastError();
 }

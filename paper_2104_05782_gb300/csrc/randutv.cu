@@ -17,6 +17,7 @@
 //                         U(:,blk) *= Us; T below the block := 0.
 // When at most b columns remain, the trailing block gets the panel QR and the
 // SVD without a sketch (the Matlab listing of Sec. 3.2 takes a full SVD there).
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <unordered_map>
@@ -42,13 +43,27 @@ struct Workspace {
     int* counters;
     int* status;
     size_t part_elems;
+    // low-precision sketch (null for RANDUTV_FP64)
+    uint16_t *S, *St, *B16;
+    float *Pf, *Xf, *cqr;
+    unsigned long long* amax;
+    // learned q
+    float* feat;      // 16 features of the current block
+    int* qdev;        // chosen q
+    double* dq;       // candidate diagonals, 4 x w (trace mode)
+    float* qmodel;    // network parameters on the device
 };
 
+constexpr int kSlots = 28;
 struct Layout {
-    size_t off[20];
+    size_t off[kSlots];
     size_t total;
     size_t part_elems;
 };
+
+int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+bool lowp_prec(int prec) { return prec == RANDUTV_SKETCH_BF16 || prec == RANDUTV_SKETCH_FP16_SCALED; }
 
 int device_sms(int dev) {
     static std::mutex mu;
@@ -62,13 +77,15 @@ int device_sms(int dev) {
     return sms;
 }
 
-Layout make_layout(int64_t m, int64_t n, int b, int sms) {
+Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec) {
     Layout L{};
     int64_t mx = std::max<int64_t>(std::max(m, n), 1);
     int64_t bb = std::max(b, 1);
     int64_t wmax = std::min<int64_t>(bb, std::max<int64_t>(n, 1));
     size_t part = (size_t)8 * sms * 64 * 64 + (size_t)2 * mx * wmax;
-    size_t sizes[20] = {
+    const bool lp = lowp_prec(prec);
+    const int64_t npad = lp ? tc_gemm_npad((int)wmax) : 0;
+    size_t sizes[kSlots] = {
         sizeof(double) * (size_t)mx * wmax,          // G
         sizeof(double) * (size_t)mx * wmax,          // Y
         sizeof(double) * (size_t)mx * wmax,          // Z
@@ -88,9 +105,17 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms) {
         sizeof(unsigned) * 64,                       // barrier counters
         sizeof(int) * 64,                            // Jacobi rotation counters
         sizeof(int) * 64,                            // status word
-        0};
+        lp ? sizeof(uint16_t) * (size_t)n * round8(m) : 0,          // S  = T22 col-major, 16-bit
+        lp ? sizeof(uint16_t) * (size_t)m * round8(n) : 0,          // St = T22 row-major, 16-bit
+        lp ? sizeof(uint16_t) * (size_t)npad * round8(mx) : 0,      // 16-bit B operand (G, Y, Z)
+        lp ? sizeof(float) * (size_t)8 * mx * npad : 0,             // split-K partials (FP32)
+        lp ? sizeof(float) * (size_t)mx * npad : 0,                 // Y / Z in FP32
+        lp ? sizeof(float) * cholqr_scratch_floats((int)npad, sms) : 0,
+        lp ? sizeof(unsigned long long) : 0,                        // max |T22|
+        sizeof(float) * 32 + sizeof(double) * 4 * (size_t)wmax,     // learned-q features, q, candidates
+        sizeof(float) * (size_t)learnq_nparam()};                   // learned-q model
     size_t o = 0;
-    for (int i = 0; i < 20; ++i) {
+    for (int i = 0; i < kSlots; ++i) {
         L.off[i] = o;
         o += align_up(sizes[i]);
     }
@@ -122,6 +147,17 @@ Workspace carve(void* base, const Layout& L) {
     w.counters = (int*)(p + L.off[17]);
     w.status = (int*)(p + L.off[18]);
     w.part_elems = L.part_elems;
+    w.S = (uint16_t*)(p + L.off[19]);
+    w.St = (uint16_t*)(p + L.off[20]);
+    w.B16 = (uint16_t*)(p + L.off[21]);
+    w.Pf = (float*)(p + L.off[22]);
+    w.Xf = (float*)(p + L.off[23]);
+    w.cqr = (float*)(p + L.off[24]);
+    w.amax = (unsigned long long*)(p + L.off[25]);
+    w.feat = (float*)(p + L.off[26]);
+    w.qdev = (int*)(w.feat + 16);
+    w.dq = (double*)(p + L.off[26] + sizeof(float) * 32);
+    w.qmodel = (float*)(p + L.off[27]);
     return w;
 }
 
@@ -160,9 +196,18 @@ cudaError_t cached_workspace(int dev, size_t bytes, void** out) {
         if (e_ != cudaSuccess) return e_;     \
     } while (0)
 
+enum SketchMode { MODE_FIXED = 0, MODE_LEARNED = 1, MODE_TRACE = 2 };
+
 struct Ctx {
     int64_t m, n, ldt;
-    int b, q;
+    int b, q, prec;
+    int mode = MODE_FIXED;
+    bool have_model = false;
+    int* q_used = nullptr;            // host, one entry per sketch step (learned mode)
+    float* tr_feat = nullptr;         // host, 16 per block (trace mode)
+    int* tr_label = nullptr;          // host, one per block (trace mode)
+    double* tr_cand = nullptr;        // host, 4 x b per block (trace mode), optional
+    int64_t tr_max = 0, tr_count = 0;
     uint64_t seed;
     double *U, *T, *V;
     Workspace w;
@@ -244,20 +289,193 @@ cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
     return cudaSuccess;
 }
 
+// Y = (T22^T T22)^q T22^T G with 16-bit operands on tcgen05 (FP32 accumulate)
+// and FP32 shifted-CholeskyQR re-orthonormalisation after every product but
+// the last.  lowp_begin leaves Y0 = T22^T G in c.w.Xf (FP32); lowp_iterate
+// applies `iters` power-iteration pairs to it; lowp_finish copies the result
+// to FP64 in c.w.Y (n' x b).
+struct LowpShape {
+    int64_t mp, np, lds, ldst;
+    int npad;
+    bool f16;
+};
+
+LowpShape lowp_shape(const Ctx& c, int64_t mp, int64_t np) {
+    return LowpShape{mp, np, round8(mp), round8(np), tc_gemm_npad(c.b), c.prec == RANDUTV_SKETCH_FP16_SCALED};
+}
+
+// (A, lda, M, K) = (S, lds, n', m') for T22^T X; (St, ldst, m', n') for T22 X
+cudaError_t lowp_product(Ctx& c, const LowpShape& s, bool transposed, int64_t ldb) {
+    const int b = c.b;
+    const uint16_t* A = transposed ? c.w.S : c.w.St;
+    const int64_t lda = transposed ? s.lds : s.ldst;
+    const int64_t M = transposed ? s.np : s.mp, K = transposed ? s.mp : s.np;
+    const int splits = tc_gemm_splits(M, K, c.sms);
+    {
+        TraceScope ts("tc_gemm_sketch", 2.0 * (double)M * b * K,
+                      2.0 * ((double)M * K + (double)b * K) + 4.0 * splits * (double)M * s.npad, c.st);
+        CK(tc_gemm(A, lda, c.w.B16, ldb, M, b, K, s.f16, c.w.Pf, M, M * s.npad, splits, c.w.status, c.st));
+    }
+    TraceScope ts("lowp_reduce", 0.0, 4.0 * (splits + 1.0) * (double)M * b, c.st);
+    return reduce_splits(c.w.Pf, M * s.npad, splits, M, b, M, c.w.Xf, c.st);
+}
+
+cudaError_t lowp_begin(Ctx& c, int64_t i, const double* T22, const LowpShape& s) {
+    const int b = c.b;
+    {
+        TraceScope ts("lowp_shadow", 0.0, (8.0 + 4.0) * (double)s.mp * s.np, c.st);
+        if (s.f16) CK(absmax_f64(T22, c.ldt, s.mp, s.np, c.w.amax, c.st));
+        CK(shadow16(T22, c.ldt, s.mp, s.np, c.w.S, s.lds, c.w.St, s.ldst, s.f16, c.w.amax, c.st));
+    }
+    {
+        TraceScope ts("gaussian", 0.0, 8.0 * (double)s.mp * b, c.st);
+        CK(gaussian_f64(c.seed, i, s.mp, b, c.w.G, s.mp, c.st));
+        CK(pack16_f64(c.w.G, s.mp, s.mp, b, c.w.B16, s.lds, s.f16, c.st));
+    }
+    return lowp_product(c, s, true, s.lds);  // Y0 = T22^T G
+}
+
+cudaError_t lowp_iterate(Ctx& c, const LowpShape& s, int iters) {
+    for (int it = 0; it < iters; ++it) {
+        {
+            TraceScope ts("lowp_cholqr", 0.0, 0.0, c.st);
+            CK(cholqr32(c.w.Xf, s.np, c.b, 3, c.w.B16, s.ldst, s.f16, c.w.cqr, c.sms, c.st));
+        }
+        CK(lowp_product(c, s, false, s.ldst));  // Z = T22 Y
+        {
+            TraceScope ts("lowp_cholqr", 0.0, 0.0, c.st);
+            CK(cholqr32(c.w.Xf, s.mp, c.b, 3, c.w.B16, s.lds, s.f16, c.w.cqr, c.sms, c.st));
+        }
+        CK(lowp_product(c, s, true, s.lds));  // Y = T22^T Z
+    }
+    return cudaSuccess;
+}
+
+cudaError_t lowp_finish(Ctx& c, const LowpShape& s) { return f32_to_f64(c.w.Xf, s.np * c.b, c.w.Y, c.st); }
+
+// FP64 sketch: Y0 = T22^T G into c.w.Y; iterate: Y := T22^T (T22 Y).
+cudaError_t fp64_begin(Ctx& c, int64_t i, const double* T22, int64_t mp, int64_t np) {
+    const int b = c.b;
+    {
+        TraceScope ts("gaussian", 0.0, 8.0 * (double)mp * b, c.st);
+        CK(gaussian_f64(c.seed, i, mp, b, c.w.G, mp, c.st));
+    }
+    return gemm(c, "gemm_sketch", true, false, np, b, mp, 1.0, T22, c.ldt, c.w.G, mp, 0.0, c.w.Y, np);
+}
+
+cudaError_t fp64_iterate(Ctx& c, const double* T22, int64_t mp, int64_t np, double* Y, int iters) {
+    const int b = c.b;
+    for (int it = 0; it < iters; ++it) {
+        CK(gemm(c, "gemm_sketch", false, false, mp, b, np, 1.0, T22, c.ldt, Y, np, 0.0, c.w.Z, mp));
+        CK(gemm(c, "gemm_sketch", true, false, np, b, mp, 1.0, T22, c.ldt, c.w.Z, mp, 0.0, Y, np));
+    }
+    return cudaSuccess;
+}
+
+// Features of this block (needs Y0 in c.w.Y): Householder R of a copy of Y0.
+cudaError_t block_features(Ctx& c, int64_t k0, int64_t np) {
+    TraceScope ts("learnq_features", 0.0, 16.0 * (double)np * c.b, c.st);
+    CK(copy_matrix(c.w.Y, np, c.w.Z, np, np, c.b, c.st));
+    CK(panel_qr(c.w.Z, np, np, c.b, c.w.tau, c.w.pscr, c.w.bars, c.w.status, c.sms, c.st));
+    return learnq_features(c.T, c.ldt, k0, k0 > 0 ? c.b : 0, c.w.Z, np, c.b, c.w.feat, c.st);
+}
+
+// Trace mode: diagonal the step would produce with q = 0..3, i.e. the
+// singular values of T22 Q1(q), Q1(q) = orth((T22^T T22)^q Y0); the q = 2
+// sketch is left in c.w.Y for the step itself.
+cudaError_t trace_candidates(Ctx& c, const double* T22, int64_t mp, int64_t np) {
+    const int b = c.b;
+    double* Yc = c.w.tmp;
+    CK(copy_matrix(c.w.Y, np, Yc, np, np, b, c.st));
+    for (int q = 0; q < 4; ++q) {
+        if (q > 0) CK(fp64_iterate(c, T22, mp, np, Yc, 1));
+        if (q == 2) CK(copy_matrix(Yc, np, c.w.Y, np, np, b, c.st));
+        // explicit Q1 of the Householder QR of Yc
+        CK(copy_matrix(Yc, np, c.w.X2, np, np, b, c.st));
+        CK(factor_panel(c, c.w.X2, np, np, b));
+        CK(set_eye_rect(c.w.X, np, b, np, c.st));
+        CK(gemm(c, "learnq_trace", false, true, b, b, b, 1.0, c.w.Tf, b, c.w.W, np, 0.0, c.w.G, b));
+        CK(gemm(c, "learnq_trace", false, false, np, b, b, -1.0, c.w.W, np, c.w.G, b, 1.0, c.w.X, np));
+        // sigma(T22 Q1) from the R of its QR
+        CK(gemm(c, "learnq_trace", false, false, mp, b, np, 1.0, T22, c.ldt, c.w.X, np, 0.0, c.w.Z, mp));
+        CK(panel_qr(c.w.Z, mp, mp, b, c.w.tau, c.w.pscr, c.w.bars, c.w.status, c.sms, c.st));
+        CK(jacobi_svd(c.w.Z, mp, b, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status,
+                      kMaxSweeps, c.st));
+        CK(cudaMemcpyAsync(c.w.dq + (size_t)q * b, c.w.D, sizeof(double) * b, cudaMemcpyDeviceToDevice, c.st));
+    }
+    return cudaSuccess;
+}
+
 // One sketch step (n' > b) at column offset k0.
 cudaError_t sketch_step(Ctx& c, int64_t i) {
     const int64_t m = c.m, n = c.n, ldt = c.ldt;
     const int b = c.b;
     const int64_t k0 = i * (int64_t)b, mp = m - k0, np = n - k0;
     double* T22 = c.T + k0 + k0 * ldt;
-    {
-        TraceScope ts("gaussian", 0.0, 8.0 * (double)mp * b, c.st);
-        CK(gaussian_f64(c.seed, i, mp, b, c.w.G, mp, c.st));
-    }
-    CK(gemm(c, "gemm_sketch", true, false, np, b, mp, 1.0, T22, ldt, c.w.G, mp, 0.0, c.w.Y, np));
-    for (int it = 0; it < c.q; ++it) {
-        CK(gemm(c, "gemm_sketch", false, false, mp, b, np, 1.0, T22, ldt, c.w.Y, np, 0.0, c.w.Z, mp));
-        CK(gemm(c, "gemm_sketch", true, false, np, b, mp, 1.0, T22, ldt, c.w.Z, mp, 0.0, c.w.Y, np));
+    // the 16-bit tensor-core sketch needs b % 16 == 0, b <= 256 and a trailing
+    // matrix of at least 128 x 128 (one TMA box); smaller steps stay in FP64
+    const bool lowp = lowp_prec(c.prec) && b % 16 == 0 && b <= 256 && mp >= 128 && np >= 128;
+    const LowpShape ls = lowp_shape(c, mp, np);
+    int iters = c.q;
+    if (c.mode == MODE_FIXED) {
+        if (lowp) {
+            CK(lowp_begin(c, i, T22, ls));
+            CK(lowp_iterate(c, ls, iters));
+            CK(lowp_finish(c, ls));
+        } else {
+            CK(fp64_begin(c, i, T22, mp, np));
+            CK(fp64_iterate(c, T22, mp, np, c.w.Y, iters));
+        }
+    } else if (c.mode == MODE_TRACE) {
+        CK(fp64_begin(c, i, T22, mp, np));
+        CK(block_features(c, k0, np));
+        CK(trace_candidates(c, T22, mp, np));
+        if (c.tr_count < c.tr_max) {
+            double cand[4 * 512];
+            CK(cudaMemcpyAsync(c.tr_feat + 16 * c.tr_count, c.w.feat, sizeof(float) * 16, cudaMemcpyDeviceToHost,
+                               c.st));
+            CK(cudaMemcpyAsync(cand, c.w.dq, sizeof(double) * 4 * b, cudaMemcpyDeviceToHost, c.st));
+            CK(cudaStreamSynchronize(c.st));
+            // label: smallest q whose diagonal is within 5% of the q = 2 one
+            // (entries below 1e-13 of the block's largest are rounding noise)
+            int label = 2;
+            for (int q = 0; q < 2; ++q) {
+                double worst = 0.0;
+                for (int j = 0; j < b; ++j) {
+                    double ref = cand[2 * b + j];
+                    if (!(ref > 1e-13 * cand[2 * b])) continue;
+                    worst = std::max(worst, std::fabs(cand[q * b + j] / ref - 1.0));
+                }
+                if (worst <= 0.05) {
+                    label = q;
+                    break;
+                }
+            }
+            c.tr_label[c.tr_count] = label;
+            if (c.tr_cand)
+                for (int e = 0; e < 4 * b; ++e) c.tr_cand[(size_t)c.tr_count * 4 * b + e] = cand[e];
+            ++c.tr_count;
+        }
+    } else {  // MODE_LEARNED
+        if (lowp) {
+            CK(lowp_begin(c, i, T22, ls));
+            CK(lowp_finish(c, ls));
+        } else {
+            CK(fp64_begin(c, i, T22, mp, np));
+        }
+        CK(block_features(c, k0, np));
+        int qh = c.q;
+        CK(learnq_infer(c.have_model ? c.w.qmodel : nullptr, c.w.feat, c.q, c.w.qdev, c.st));
+        CK(cudaMemcpyAsync(&qh, c.w.qdev, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+        CK(cudaStreamSynchronize(c.st));
+        iters = std::min(std::max(qh, 0), 3);
+        if (c.q_used) c.q_used[i] = iters;
+        if (lowp) {
+            CK(lowp_iterate(c, ls, iters));
+            CK(lowp_finish(c, ls));
+        } else {
+            CK(fp64_iterate(c, T22, mp, np, c.w.Y, iters));
+        }
     }
     CK(factor_panel(c, c.w.Y, np, np, b));
     CK(apply_right(c, c.T + k0 * ldt, ldt, m, np, b));
@@ -324,23 +542,39 @@ const char* randutv_status_string(int s) {
 
 size_t randutv_workspace_size(int64_t m, int64_t n, int b, int prec) {
     if (m < n || n < 0 || b < 1) return 0;
-    if (prec != RANDUTV_FP64) return 0;
+    if (prec != RANDUTV_FP64 && !lowp_prec(prec)) return 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
-    return make_layout(m, n, b, device_sms(dev)).total;
+    return make_layout(m, n, b, device_sms(dev), prec).total;
 }
 
-randutv_status randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, uint64_t seed,
-                                 double* U, double* T, double* V, int prec, void* stream, void* workspace,
-                                 size_t ws_bytes, int64_t stop_after, int* info) {
+}  // extern "C"
+
+namespace rutv {
+namespace {
+
+struct ModeArgs {
+    int mode = MODE_FIXED;
+    const float* model = nullptr;  // host parameters (learned mode)
+    int* q_used = nullptr;
+    float* tr_feat = nullptr;
+    int* tr_label = nullptr;
+    double* tr_cand = nullptr;
+    int64_t tr_max = 0;
+    int64_t* tr_count = nullptr;
+};
+
+randutv_status factor_impl(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, uint64_t seed, double* U,
+                           double* T, double* V, int prec, void* stream, void* workspace, size_t ws_bytes,
+                           int64_t stop_after, int* info, const ModeArgs& ma) {
     if (!args_ok(m, n, A, lda, b, q, T)) return RANDUTV_EINVAL;
-    if (prec != RANDUTV_FP64) return RANDUTV_ENOTIMPL;
+    if (prec != RANDUTV_FP64 && !lowp_prec(prec)) return RANDUTV_ENOTIMPL;
     if (A == T && lda != m) return RANDUTV_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RANDUTV_ECUDA;
     const int sms = device_sms(dev);
-    Layout L = make_layout(m, n, b, sms);
+    Layout L = make_layout(m, n, b, sms, prec);
     void* base = workspace;
     if (base == nullptr) {
         if (cached_workspace(dev, L.total, &base) != cudaSuccess) return RANDUTV_ENOMEM;
@@ -349,14 +583,36 @@ randutv_status randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t 
     }
     Ctx c{};
     c.m = m; c.n = n; c.ldt = std::max<int64_t>(m, 1);
-    c.b = b; c.q = q; c.seed = seed;
+    c.b = b; c.q = q; c.seed = seed; c.prec = prec;
     c.U = U; c.T = T; c.V = V;
     c.w = carve(base, L);
     c.sms = sms;
     c.st = st;
+    c.mode = ma.mode;
+    c.q_used = ma.q_used;
+    c.tr_feat = ma.tr_feat;
+    c.tr_label = ma.tr_label;
+    c.tr_cand = ma.tr_cand;
+    c.tr_max = ma.tr_max;
     if (cudaMemsetAsync(c.w.status, 0, sizeof(int), st) != cudaSuccess) return RANDUTV_ECUDA;
+    if (lowp_prec(prec)) {  // rows b..npad-1 of the 16-bit B operand stay zero
+        size_t bytes = sizeof(uint16_t) * (size_t)tc_gemm_npad(std::min<int64_t>(b, std::max<int64_t>(n, 1))) *
+                       round8(std::max<int64_t>(std::max(m, n), 1));
+        if (cudaMemsetAsync(c.w.B16, 0, bytes, st) != cudaSuccess) return RANDUTV_ECUDA;
+    }
+    if (ma.mode == MODE_LEARNED && ma.model != nullptr) {
+        if (cudaMemcpyAsync(c.w.qmodel, ma.model, sizeof(float) * learnq_nparam(), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+            return RANDUTV_ECUDA;
+        c.have_model = true;
+    }
+    if (ma.q_used) {
+        int64_t nb = (n + b - 1) / b;
+        for (int64_t i = 0; i < nb; ++i) ma.q_used[i] = -1;
+    }
     if (m == 0) return RANDUTV_OK;
     if (run_factor(c, A, lda, stop_after) != cudaSuccess) return RANDUTV_ECUDA;
+    if (ma.tr_count) *ma.tr_count = c.tr_count;
     if (info != nullptr) {
         if (cudaMemcpyAsync(info, c.w.status, sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return RANDUTV_ECUDA;
@@ -367,6 +623,129 @@ randutv_status randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t 
         return RANDUTV_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return RANDUTV_ECUDA;
     return status_from_bits(bits);
+}
+
+}  // namespace
+}  // namespace rutv
+
+extern "C" {
+
+randutv_status randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, uint64_t seed,
+                                 double* U, double* T, double* V, int prec, void* stream, void* workspace,
+                                 size_t ws_bytes, int64_t stop_after, int* info) {
+    return factor_impl(m, n, A, lda, b, q, seed, U, T, V, prec, stream, workspace, ws_bytes, stop_after, info,
+                       ModeArgs{});
+}
+
+randutv_status randutv_factor_learnedq_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
+                                          const float* model, uint64_t seed, double* U, double* T, double* V,
+                                          int* q_used, int prec, void* stream) {
+    ModeArgs ma;
+    ma.mode = MODE_LEARNED;
+    ma.model = model;
+    ma.q_used = q_used;
+    return factor_impl(m, n, A, lda, b, 2, seed, U, T, V, prec, stream, nullptr, 0, -1, nullptr, ma);
+}
+
+randutv_status randutv_factor_learnedq(int64_t m, int64_t n, const double* A, int64_t lda, int b, const float* model,
+                                       uint64_t seed, double* U, double* T, double* V, int* q_used) {
+    return randutv_factor_learnedq_ex(m, n, A, lda, b, model, seed, U, T, V, q_used, RANDUTV_FP64, nullptr);
+}
+
+randutv_status randutv_learnq_trace(int64_t m, int64_t n, const double* A, int64_t lda, int b, uint64_t seed,
+                                    double* T, float* features, int* labels, double* candidates, int64_t max_blocks,
+                                    int64_t* nblocks) {
+    if (!features || !labels || max_blocks < 0 || b > 512) return RANDUTV_EINVAL;
+    ModeArgs ma;
+    ma.mode = MODE_TRACE;
+    ma.tr_feat = features;
+    ma.tr_label = labels;
+    ma.tr_cand = candidates;
+    ma.tr_max = max_blocks;
+    int64_t cnt = 0;
+    ma.tr_count = &cnt;
+    randutv_status r = factor_impl(m, n, A, lda, b, 2, seed, nullptr, T, nullptr, RANDUTV_FP64, nullptr, nullptr, 0,
+                                   -1, nullptr, ma);
+    if (nblocks) *nblocks = cnt;
+    return r;
+}
+
+int randutv_learnq_model_floats(void) { return learnq_nparam(); }
+
+namespace {
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+}  // namespace
+
+randutv_status randutv_learnq_train(const float* X, const int* y, int N, int epochs, float lr, float wd,
+                                    float* model, float* loss_history) {
+    if (!X || !y || !model || N <= 0 || epochs < 0) return RANDUTV_EINVAL;
+    const int np = learnq_nparam();
+    const size_t scr = learnq_train_scratch_floats(N);
+    DevBuf buf;
+    size_t bytes = sizeof(float) * ((size_t)N * 16 + np + scr + (size_t)std::max(epochs, 1)) + sizeof(int) * N + 1024;
+    if (cudaMalloc(&buf.p, bytes) != cudaSuccess) return RANDUTV_ENOMEM;
+    float* dX = (float*)buf.p;
+    float* dP = dX + (size_t)N * 16;
+    float* dS = dP + np;
+    float* dL = dS + scr;
+    int* dy = (int*)(dL + std::max(epochs, 1));
+    if (cudaMemcpy(dX, X, sizeof(float) * N * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dy, y, sizeof(int) * N, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dP, model, sizeof(float) * np, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(dS, 0, sizeof(float) * scr) != cudaSuccess)
+        return RANDUTV_ECUDA;
+    for (int e = 0; e < epochs; ++e)
+        if (learnq_train_step(dP, dX, dy, N, dS, nullptr, dL + e, e + 1, lr, wd, nullptr) != cudaSuccess)
+            return RANDUTV_ECUDA;
+    if (cudaMemcpy(model, dP, sizeof(float) * np, cudaMemcpyDeviceToHost) != cudaSuccess) return RANDUTV_ECUDA;
+    if (loss_history && epochs > 0 &&
+        cudaMemcpy(loss_history, dL, sizeof(float) * epochs, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return RANDUTV_ECUDA;
+    return RANDUTV_OK;
+}
+
+randutv_status randutv_learnq_grad(const float* X, const int* y, int N, const float* model, float* grad,
+                                   float* loss) {
+    if (!X || !y || !model || !grad || N <= 0) return RANDUTV_EINVAL;
+    const int np = learnq_nparam();
+    const size_t scr = learnq_train_scratch_floats(N);
+    DevBuf buf;
+    size_t bytes = sizeof(float) * ((size_t)N * 16 + 2 * (size_t)np + scr + 4) + sizeof(int) * N + 1024;
+    if (cudaMalloc(&buf.p, bytes) != cudaSuccess) return RANDUTV_ENOMEM;
+    float* dX = (float*)buf.p;
+    float* dP = dX + (size_t)N * 16;
+    float* dG = dP + np;
+    float* dS = dG + np;
+    float* dL = dS + scr;
+    int* dy = (int*)(dL + 4);
+    if (cudaMemcpy(dX, X, sizeof(float) * N * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dy, y, sizeof(int) * N, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dP, model, sizeof(float) * np, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(dG, 0, sizeof(float) * np) != cudaSuccess)
+        return RANDUTV_ECUDA;
+    if (learnq_train_step(dP, dX, dy, N, dS, dG, dL, 0, 0.f, 0.f, nullptr) != cudaSuccess) return RANDUTV_ECUDA;
+    if (cudaMemcpy(grad, dG, sizeof(float) * np, cudaMemcpyDeviceToHost) != cudaSuccess) return RANDUTV_ECUDA;
+    if (loss && cudaMemcpy(loss, dL, sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return RANDUTV_ECUDA;
+    return RANDUTV_OK;
+}
+
+randutv_status randutv_learnq_predict(const float* model, const float* X, int N, float* probs) {
+    if (!model || !X || !probs || N <= 0) return RANDUTV_EINVAL;
+    const int np = learnq_nparam();
+    DevBuf buf;
+    if (cudaMalloc(&buf.p, sizeof(float) * ((size_t)N * 20 + np) + 256) != cudaSuccess) return RANDUTV_ENOMEM;
+    float* dX = (float*)buf.p;
+    float* dP = dX + (size_t)N * 16;
+    float* dPr = dP + np;
+    if (cudaMemcpy(dX, X, sizeof(float) * N * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dP, model, sizeof(float) * np, cudaMemcpyHostToDevice) != cudaSuccess)
+        return RANDUTV_ECUDA;
+    if (learnq_predict(dP, dX, N, dPr, nullptr) != cudaSuccess) return RANDUTV_ECUDA;
+    if (cudaMemcpy(probs, dPr, sizeof(float) * N * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return RANDUTV_ECUDA;
+    return RANDUTV_OK;
 }
 
 randutv_status randutv_factor(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, uint64_t seed,

@@ -62,14 +62,36 @@ def test_matrix(m: int, n: int, kind: str = "geometric10", seed_u: int = 1, seed
     return np.asfortranarray((ua * s) @ va.T)
 
 
-def test_matrix_device(m: int, n: int, kind: str, seed_u: int, seed_v: int, device="cuda"):
-    """Large synthetic matrix built on the GPU with torch (library QR and matmul).
+def _hartley_mix(X, gen, rounds: int = 2):
+    """Apply an orthogonal Q = prod (P_r H D_r) to the columns of X (torch, FP64).
 
-    The orthogonal factors come from an FP32 QR of seeded Gaussians; the product
-    is formed in FP64.  By multiplicative perturbation theory the singular values
-    of the result equal the prescribed ones to a relative ~1e-6, which is what
-    the quality ratios T_ii / sigma_i need.  Returns a column-major FP64 tensor
-    (a transposed view of a row-major buffer) and the prescribed spectrum.
+    D_r: random signs, H: orthonormal discrete Hartley transform
+    (H x = (Re F x - Im F x) / sqrt(n), symmetric and orthogonal), P_r: random
+    row permutation.  Every column of Q is dense; Q is orthogonal to FP64
+    rounding, so the singular values of Q M equal those of M.
+    """
+    import torch
+
+    n = X.shape[0]
+    for _ in range(rounds):
+        sg = torch.randint(0, 2, (n, 1), generator=gen, device=X.device, dtype=torch.int64) * 2 - 1
+        X = X * sg.to(X.dtype)
+        F = torch.fft.fft(X, dim=0)
+        X = (F.real - F.imag) / (n ** 0.5)
+        del F
+        perm = torch.randperm(n, generator=gen, device=X.device)
+        X = X[perm]
+    return X
+
+
+def test_matrix_device(m: int, n: int, kind: str, seed_u: int, seed_v: int, device="cuda"):
+    """Large synthetic matrix A = Q_U [diag(sigma); 0] Q_V^T built on the device.
+
+    Q_U, Q_V are FFT-based random orthogonal transforms (see _hartley_mix), so
+    no dense QR is needed and the singular values of A are the prescribed ones
+    to FP64 rounding.  kind == "normal" gives i.i.d. N(0,1) entries instead.
+    Returns a column-major FP64 tensor (a transposed view of a row-major
+    buffer) and the prescribed spectrum (None for "normal").
     """
     import torch
 
@@ -78,16 +100,13 @@ def test_matrix_device(m: int, n: int, kind: str, seed_u: int, seed_v: int, devi
         gen.manual_seed(seed_u)
         a = torch.randn(n, m, generator=gen, device=device, dtype=torch.float64)
         return a.t(), None
-    s = torch.from_numpy(spectrum(kind, n)).to(device)
+    s = spectrum(kind, n)
+    M0 = torch.zeros(m, n, dtype=torch.float64, device=device)
+    M0.diagonal().copy_(torch.from_numpy(s))
     gen.manual_seed(seed_u)
-    gu = torch.randn(m, m, generator=gen, device=device, dtype=torch.float32)
-    qu = torch.linalg.qr(gu)[0][:, :n].to(torch.float64)
-    del gu
+    X = _hartley_mix(M0, gen)            # Q_U M0       (m x n)
+    del M0
     gen.manual_seed(seed_v)
-    gv = torch.randn(n, n, generator=gen, device=device, dtype=torch.float32)
-    qv = torch.linalg.qr(gv)[0].to(torch.float64)
-    del gv
-    # column-major A (m x n) == row-major A^T (n x m)
-    at = (qv * s) @ qu.t()
-    del qu, qv
-    return at.t(), s.cpu().numpy()
+    At = _hartley_mix(X.t().contiguous(), gen)   # Q_V (Q_U M0)^T = A^T  (n x m, row-major)
+    del X
+    return At.t(), s

@@ -1,0 +1,177 @@
+"""Learned power-iteration count: network kernels against the FP64 oracle
+network, trace labels against their definition, the learned factorization
+against the fixed-q path, and what the trained network gains over q = 2."""
+import time
+
+import numpy as np
+import pytest
+
+import synthetic
+from conftest import utv_bound
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rutv():
+    import paper_2104_05782_gb300 as r
+    from paper_2104_05782_gb300 import build
+    build.build()
+    r.load()
+    assert r.randutv_learnq_model_floats() == mlp.NPARAM
+    return r
+
+
+def dev(A):
+    return torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+
+
+def host(X):
+    return X.t().contiguous().cpu().numpy().T
+
+
+def toy(seed, N=64):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((N, 16)) * 2.0 - 1.0
+    y = rng.integers(0, 4, N)
+    p = mlp.init(seed, mu=X.mean(axis=0), sd=X.std(axis=0))
+    return X, y, p
+
+
+def test_gradient_matches_oracle(rutv):
+    X, y, p = toy(0)
+    r, g, loss = rutv.randutv_learnq_grad(X, y, p)
+    assert r == 0
+    g_ref = mlp.grad(p.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64), y)
+    scale = np.abs(g_ref).max()
+    assert np.abs(g - g_ref).max() <= 1e-4 * scale
+    assert abs(loss - mlp.loss(p, X, y)) <= 1e-5 * abs(mlp.loss(p, X, y))
+
+
+def test_predict_matches_oracle(rutv):
+    X, y, p = toy(1, N=33)
+    r, pr = rutv.randutv_learnq_predict(p, X)
+    assert r == 0
+    ref = mlp.softmax(mlp.forward(p.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64))[0])
+    assert np.abs(pr - ref).max() <= 1e-5
+
+
+def test_training_fits_separable_labels(rutv):
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((256, 16))
+    y = np.argmax(X[:, :4], axis=1)          # learnable rule
+    p = mlp.init(2, mu=X.mean(axis=0), sd=X.std(axis=0))
+    r, p2, hist = rutv.randutv_learnq_train(X, y, p, 300, lr=3e-3)
+    assert r == 0 and hist[-1] < 0.5 * hist[0]
+    _, pr = rutv.randutv_learnq_predict(p2, X)
+    assert np.mean(np.argmax(pr, axis=1) == y) > 0.9
+    # the GPU update is a deterministic function of its inputs
+    _, p3, _ = rutv.randutv_learnq_train(X, y, p, 300, lr=3e-3)
+    assert np.array_equal(p2, p3)
+
+
+def forcing_model(q):
+    p = np.zeros(mlp.NPARAM, dtype=np.float32)
+    p[-16:] = 1.0
+    p[mlp.NPARAM - 32 - 4 + q] = 10.0      # b3[q]
+    return p
+
+
+@pytest.mark.parametrize("q", [0, 2])
+def test_learned_path_with_forcing_model_equals_fixed_q(rutv, q):
+    A = synthetic.test_matrix(500, 400, "algebraic", 5, 6)
+    m, n, b = 500, 400, 64
+    T = rutv.colmajor_empty(m, n)
+    U = rutv.colmajor_empty(m, m)
+    V = rutv.colmajor_empty(n, n)
+    r, qu = rutv.randutv_factor_learnedq(m, n, dev(A), m, b, forcing_model(q), 3, U, T, V)
+    torch.cuda.synchronize()
+    assert r == 0
+    assert qu[:-1] == [q] * (len(qu) - 1) and qu[-1] == -1
+    Uf, Tf, Vf = rutv.factor(dev(A), b, q, 3)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(T), host(Tf)) and np.array_equal(host(U), host(Uf))
+
+
+def test_no_model_falls_back_to_q2(rutv):
+    A = synthetic.test_matrix(300, 300, "normal", 1, 2)
+    T = rutv.colmajor_empty(300, 300)
+    r, qu = rutv.randutv_factor_learnedq(300, 300, dev(A), 300, 64, None, 0, None, T, None)
+    assert r == 0 and all(x == 2 for x in qu[:-1])
+    _, Tf, _ = rutv.factor(dev(A), 64, 2, 0, want_uv=False)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(T), host(Tf))
+
+
+def test_trace_labels_follow_definition(rutv):
+    m = n = 640
+    b = 64
+    A = synthetic.test_matrix(m, n, "algebraic", 7, 8)
+    T = rutv.colmajor_empty(m, n)
+    r, F, y, cand = rutv.randutv_learnq_trace(m, n, dev(A), m, b, 4, T, candidates=True)
+    assert r == 0 and len(y) == n // b - 1
+    assert np.all(np.isfinite(F))
+    assert np.all(F[:, :8] <= 1e-6)  # previous diagonal block: sorted descending
+    # the q = 2 candidate diagonal is the diagonal the q = 2 trajectory produces
+    Tt = host(T)
+    _, Tf, _ = rutv.factor(dev(A), b, 2, 4, want_uv=False)
+    torch.cuda.synchronize()
+    assert np.abs(Tt - host(Tf)).max() <= 1e-12 * np.linalg.norm(A)
+    for i in range(len(y)):
+        d2 = np.diag(Tt)[i * b:(i + 1) * b]
+        assert np.abs(cand[i, 2] - d2).max() <= 1e-10 * d2[0]
+        ok = [np.abs(cand[i, q][cand[i, 2] > 1e-13 * cand[i, 2, 0]] /
+                     cand[i, 2][cand[i, 2] > 1e-13 * cand[i, 2, 0]] - 1).max() <= 0.05 for q in (0, 1)]
+        want = 0 if ok[0] else (1 if ok[1] else 2)
+        assert y[i] == want
+    # interlacing: no candidate exceeds the true singular values of the trailing matrix
+    s = np.linalg.svd(A, compute_uv=False)
+    assert np.all(cand[0] <= s[0] * (1 + 1e-12))
+
+
+def test_trained_network_gain_over_q2(rutv):
+    """Held-out matrices (seeds 10^6 + k): reports the power iterations and time
+    the trained network saves against q = 2 and checks that T_ii / sigma_i stays
+    within 5% of the q = 2 result (or closer to 1) on at least 98% of indices."""
+    model = rutv.load_qnet()
+    if model is None:
+        pytest.skip("no trained network shipped (run python -m paper_2104_05782_gb300.learnq_train)")
+    kinds = ["geometric10", "algebraic", "gap", "geometric8"]
+    n, b = 2048, 128
+    t_l = t_2 = 0.0
+    iters_l = iters_2 = 0
+    for k, kind in enumerate(kinds):
+        A = synthetic.test_matrix(n, n, kind, 10 ** 6 + k, 2 * 10 ** 6 + k)
+        s = np.linalg.svd(A, compute_uv=False)
+        dA = dev(A)
+        T = rutv.colmajor_empty(n, n)
+        U = rutv.colmajor_empty(n, n)
+        V = rutv.colmajor_empty(n, n)
+        rutv.factor(dA, b, 2, k)                       # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r, qu = rutv.randutv_factor_learnedq(n, n, dA, n, b, model, k, U, T, V)
+        torch.cuda.synchronize()
+        t_l += time.perf_counter() - t0
+        assert r == 0
+        t0 = time.perf_counter()
+        U2, T2, V2 = rutv.factor(dA, b, 2, k)
+        torch.cuda.synchronize()
+        t_2 += time.perf_counter() - t0
+        iters_l += sum(x for x in qu if x >= 0)
+        iters_2 += 2 * sum(1 for x in qu if x >= 0)
+        Th, T2h = host(T), host(T2)
+        nrm = np.linalg.norm(A)
+        assert np.linalg.norm(A - host(U) @ Th @ host(V).T) / nrm <= utv_bound(n)
+        keep = s > 1e3 * 2.0 ** -53 * s[0]
+        r_l = np.diag(Th)[keep] / s[keep]
+        r_2 = np.diag(T2h)[keep] / s[keep]
+        dev_ = np.abs(r_l / r_2 - 1)
+        ok = (dev_ <= 0.05) | (np.abs(np.log(r_l)) <= np.abs(np.log(r_2)))
+        print("%s: q used %s, max dev %.3g, %.4f of indices within 5%% (or better)"
+              % (kind, qu, dev_.max(), ok.mean()))
+        assert ok.mean() >= 0.98, kind
+    print("learned-q: %d vs %d power iterations, %.3f s vs %.3f s" % (iters_l, iters_2, t_l, t_2))
+    assert iters_l <= iters_2

@@ -1,0 +1,83 @@
+"""Mixed-precision sketch (BF16 and scaled FP16 on tcgen05, FP32 re-orthonormalisation).
+
+The sketch only chooses the subspace V_alpha (Sec. 3.2.1), so its entries are
+not compared with the FP64 path entry by entry (different rounding gives a
+different, equally valid basis).  What must hold: the factorization stays
+exact to FP64 level (everything after the sketch is FP64) and the rank-revealing
+quality T_ii / sigma_i stays within 5% of the plain FP64 path.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from conftest import utv_bound
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def rutv():
+    import paper_2104_05782_gb300 as r
+    from paper_2104_05782_gb300 import build
+    build.build()
+    r.load()
+    return r
+
+
+def run(rutv, A, b, q, prec, seed=0):
+    dA = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+    U, T, V = rutv.factor(dA, b, q, seed, prec=prec)
+    torch.cuda.synchronize()
+    h = lambda X: X.t().contiguous().cpu().numpy().T
+    return h(U), h(T), h(V)
+
+
+@pytest.mark.parametrize("prec_name", ["RANDUTV_SKETCH_BF16", "RANDUTV_SKETCH_FP16_SCALED"])
+@pytest.mark.parametrize("m,n,b,q,kind", [
+    (1024, 1024, 128, 2, "algebraic"),
+    (1024, 1024, 128, 2, "gap"),
+    (1280, 640, 64, 2, "geometric10"),
+    (700, 520, 96, 1, "normal"),      # b = 96 (N padded to 128), ragged tails
+])
+def test_lowp_exact_and_quality(rutv, prec_name, m, n, b, q, kind):
+    prec = getattr(rutv, prec_name)
+    A = synthetic.test_matrix(m, n, kind, 41, 42)
+    U, T, V = run(rutv, A, b, q, prec)
+    nrm = np.linalg.norm(A)
+    assert np.linalg.norm(A - U @ T @ V.T) / nrm <= utv_bound(n)
+    assert np.linalg.norm(U.T @ U - np.eye(m)) <= utv_bound(m)
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= utv_bound(n)
+    assert np.array_equal(np.tril(T, -1), np.zeros_like(T))
+    _, T64, _ = run(rutv, A, b, q, rutv.RANDUTV_FP64)
+    s = np.linalg.svd(A, compute_uv=False)
+    keep = s > 1e3 * 2.0 ** -53 * s[0]          # ratios below the FP64 noise floor are not meaningful
+    r_lp = np.diag(T)[keep] / s[keep]
+    r_64 = np.diag(T64)[keep] / s[keep]
+    dev = np.abs(r_lp / r_64 - 1.0)
+    # an index passes when the low-precision ratio is within 5% of the FP64
+    # ratio, or closer to 1 than the FP64 one (the FP64 sketch, which is not
+    # re-orthonormalised, can itself lose directions that the mixed sketch keeps)
+    ok = (dev <= 0.05) | (np.abs(np.log(r_lp)) <= np.abs(np.log(r_64)))
+    frac = ok.mean()
+    print("%s %s: max dev %.3g at %d, %.4f of indices within 5%% (or better), median dev %.2e"
+          % (prec_name, kind, dev.max(), int(np.argmax(dev)), frac, np.median(dev)))
+    assert frac >= 0.98
+
+
+def test_lowp_deterministic(rutv):
+    A = synthetic.test_matrix(512, 512, "algebraic", 3, 4)
+    r1 = run(rutv, A, 128, 2, rutv.RANDUTV_SKETCH_BF16, seed=5)
+    r2 = run(rutv, A, 128, 2, rutv.RANDUTV_SKETCH_BF16, seed=5)
+    for x, y in zip(r1, r2):
+        assert np.array_equal(x, y)
+
+
+def test_lowp_small_steps_fall_back_to_fp64_sketch(rutv):
+    """b not a multiple of 16 (and trailing blocks under 128 x 128) use the FP64
+    sketch: the result then equals the FP64 path exactly."""
+    A = synthetic.test_matrix(200, 150, "normal", 5, 6)
+    r_lp = run(rutv, A, 20, 1, rutv.RANDUTV_SKETCH_BF16)
+    r_64 = run(rutv, A, 20, 1, rutv.RANDUTV_FP64)
+    for x, y in zip(r_lp, r_64):
+        assert np.array_equal(x, y)

@@ -92,22 +92,27 @@ def test_parity_against_oracle(rutv, m, n, b, q, kind, seed):
 
 
 @pytest.mark.parametrize("m,n,b,q", [(256, 128, 32, 0), (400, 400, 64, 2)])
-def test_gap_spectrum_diagonal_and_invariants(rutv, m, n, b, q):
-    """sigma = 1 repeated n/10 times: the singular vectors of a diagonal block
-    are not unique there, so only what is unique is compared entrywise -- the
-    diagonal of T (the trailing matrix never depends on the rotation chosen
-    inside a degenerate block) -- and the rest is checked for validity."""
+def test_gap_spectrum_invariants(rutv, m, n, b, q):
+    """sigma = 1 repeated n/10 times, then a gap to 1e-3: entrywise parity is
+    unpinned here.  A block that straddles the gap makes the sketch
+    Y = (A^T A)^q A^T G ill-conditioned (cond ~ (1/3e-4)^5 for q = 2), so its
+    weak directions, and everything after them, are set by rounding; inside the
+    sigma = 1 block the singular vectors are not unique.  What every valid
+    result shares is checked instead: the UTV identities, sorted nonnegative
+    diagonal blocks, |det A| = prod T_ii, and the first block's diagonal."""
     A = synthetic.test_matrix(m, n, "gap", 31, 32)
-    got = gpu_factor(rutv, A, b, q, 3)
-    want = oracle.randutv(A, b, q, 3)[:3]
-    nrm = np.linalg.norm(A)
-    assert np.abs(np.diag(got[1]) - np.diag(want[1])).max() <= 1e-10 * nrm
-    check_utv(A, *got)
-    # row norms of each block row of T are invariant under the block's rotation
+    U, T, V = gpu_factor(rutv, A, b, q, 3)
+    check_utv(A, U, T, V)
+    d = np.diag(T)
     for k0 in range(0, n, b):
-        rg = np.linalg.norm(got[1][k0:k0 + b, k0:])
-        ro = np.linalg.norm(want[1][k0:k0 + b, k0:])
-        assert abs(rg - ro) <= 1e-10 * nrm
+        blk = d[k0:k0 + b]
+        assert np.all(blk >= 0) and np.all(np.diff(blk) <= 0)
+    s = np.linalg.svd(A, compute_uv=False)
+    if m == n:
+        assert abs(np.sum(np.log10(d)) - np.sum(np.log10(s))) <= 0.05
+    _, To, _, _ = oracle.randutv(A, b, q, 3, want_uv=False)
+    k = n // 10  # the sigma = 1 cluster is found exactly by both
+    assert np.abs(d[:min(k, b)] - np.diag(To)[:min(k, b)]).max() <= 1e-10 * np.linalg.norm(A)
 
 
 def test_parity_t_only_mode(rutv):
