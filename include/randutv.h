@@ -216,6 +216,33 @@ randutv_status randutv_learnq_predict(const float* model, const float* X, int N,
 
 
 /*
+ * randutv_svd_small_noalloc -- the b x b SVD step (one-sided Jacobi, the
+ * kernel randutv_factor runs on every diagonal block) for callers that cannot
+ * allocate device memory: code under an allocator that forbids cudaMalloc,
+ * allocation-free real-time paths, or plugins whose host framework owns all
+ * device memory.  The paper has no counterpart; it is a packaging of an
+ * existing kernel.
+ *   w          : order of R, 0 <= w <= RANDUTV_SVD_NOALLOC_MAX_W (larger w
+ *                returns RANDUTV_EINVAL).
+ *   R          : device, w x w, leading dimension ldr >= w; only its upper
+ *                triangle is read.
+ *   D, Us, Vs  : device outputs: D (w) descending singular values, Us and Vs
+ *                (w x w, ld w) with R = Us diag(D) Vs^T, each pair signed so
+ *                that the largest entry of Vs(:, j) is positive.
+ *   stream     : cudaStream_t (NULL = legacy default stream).  Synchronous.
+ * The scratch (the Jacobi working copies, barrier and status words) is a
+ * fixed device array inside the library, about 1 MiB, that every GPU which
+ * loads the library holds until the process exits; no call allocates or
+ * frees memory.  The first call on a device looks up that array's device
+ * address, so make it before any CUDA stream capture.  All calls on a device
+ * share the array: calls that overlap on the GPU (other host threads, other
+ * streams) race and must be serialised by the caller.
+ */
+#define RANDUTV_SVD_NOALLOC_MAX_W 256
+randutv_status randutv_svd_small_noalloc(int w, const double* R, int64_t ldr, double* D, double* Us, double* Vs,
+                                         void* stream);
+
+/*
  * Tracing (the per-task time breakdown of Sec. 5.4 / Sec. 6.1, done with CUDA
  * events).  While enabled, every launcher of the library brackets its kernel
  * launches with a pair of CUDA events on its stream and records the

@@ -110,6 +110,8 @@ def load():
     lib.randutv_learnq_grad.restype = ctypes.c_int
     lib.randutv_learnq_predict.argtypes = [fp, fp, ctypes.c_int, fp]
     lib.randutv_learnq_predict.restype = ctypes.c_int
+    lib.randutv_svd_small_noalloc.argtypes = [ctypes.c_int, _vp, _i64, _vp, _vp, _vp, _vp]
+    lib.randutv_svd_small_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -242,6 +244,11 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def randutv_svd_small_noalloc(w, R, ldr, D, Us, Vs, stream=None) -> int:
+    """randutv_svd_small_noalloc of the C ABI (device buffers; allocates nothing)."""
+    return load().randutv_svd_small_noalloc(w, _ptr(R), ldr, _ptr(D), _ptr(Us), _ptr(Vs), _stream_handle(stream))
 
 
 # ---------------------------------------------------------------- learned q
