@@ -54,7 +54,11 @@ typedef enum {
     RANDUTV_FP64 = 0,               /* every step in FP64 (DMMA tensor cores) */
     RANDUTV_SKETCH_BF16 = 1,        /* sketch and power iteration in BF16 on tcgen05, FP32 accumulate */
     RANDUTV_SKETCH_FP16_SCALED = 2, /* as BF16 with FP16 operands and a per-step scale */
-    RANDUTV_SKETCH_FP32 = 3         /* sketch in FP32 (CUDA cores); used by the batched path */
+    RANDUTV_SKETCH_FP32 = 3,        /* sketch in FP32 (CUDA cores); used by the batched path */
+    RANDUTV_FP64_EMULATED = 4,      /* every FP64 product emulated on BF16 tensor cores (Ozaki scheme,
+                                       7 x 7-bit digits, exact FP32 chunks, double-float accumulation);
+                                       panels, T factors and the small SVD stay FP64 */
+    RANDUTV_EMULATED_SKETCH_BF16 = 5 /* RANDUTV_FP64_EMULATED with the BF16 sketch of RANDUTV_SKETCH_BF16 */
 } randutv_precision;
 
 /* Human-readable name of a status code (static string). */
@@ -169,7 +173,7 @@ randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64
  *             A non-finite network output also falls back to q = 2.  The
  *             network predicts a distribution over the smallest adequate q;
  *             the step runs the smallest q whose cumulative predicted
- *             probability reaches 0.9.
+ *             probability reaches 0.95.
  *   q_used  : HOST array of ceil(n / b) ints (or NULL): the q chosen per
  *             sketch step, -1 for the final block (no sketch).
  * Other arguments as randutv_factor / randutv_factor_ex.  Synchronises the
@@ -213,7 +217,6 @@ randutv_status randutv_learnq_train(const float* X, const int* y, int N, int epo
 randutv_status randutv_learnq_grad(const float* X, const int* y, int N, const float* model, float* grad,
                                    float* loss);
 randutv_status randutv_learnq_predict(const float* model, const float* X, int N, float* probs);
-
 
 /*
  * randutv_svd_small_noalloc -- the b x b SVD step (one-sided Jacobi, the

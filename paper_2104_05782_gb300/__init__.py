@@ -26,6 +26,8 @@ RANDUTV_FP64 = 0
 RANDUTV_SKETCH_BF16 = 1
 RANDUTV_SKETCH_FP16_SCALED = 2
 RANDUTV_SKETCH_FP32 = 3
+RANDUTV_FP64_EMULATED = 4
+RANDUTV_EMULATED_SKETCH_BF16 = 5
 
 _lib = None
 _i64 = ctypes.c_int64

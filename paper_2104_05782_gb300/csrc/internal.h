@@ -80,6 +80,13 @@ size_t learnq_train_scratch_floats(int N);
 cudaError_t learnq_train_step(float* P, const float* X, const int* y, int N, float* scratch, float* grads_out,
                               float* loss_out, int t, float lr, float wd, cudaStream_t st);
 cudaError_t learnq_predict(const float* P, const float* X, int N, float* probs, cudaStream_t st);
+// ---- FP64 products emulated on BF16 tensor cores (oz_gemm.cu) ---------------
+int64_t oz_ldq(int64_t K);
+size_t oz_work_bytes(int64_t M, int64_t N, int64_t K);
+// Needs M >= 128, N >= 64, K >= 64; `work` holds oz_work_bytes(M, N, K) bytes.
+cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+                    const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work, int* status,
+                    cudaStream_t st);
 cudaError_t set_eye_rect(double* X, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st);
 
 }  // namespace rutv

@@ -26,7 +26,7 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NI * NH, OFF_W2 = OFF_B1 + NH, OFF_B
               OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NH * NO, OFF_MU = OFF_B3 + NO, OFF_SD = OFF_MU + NI,
               NPARAM = OFF_SD + NI;
 constexpr int NTRAIN = OFF_MU;  // trainable parameters (mu, sd are fixed)
-constexpr float kLearnqConfidence = 0.9f;
+constexpr float kLearnqConfidence = 0.95f;
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_d(float x) {

@@ -1,0 +1,471 @@
+// oz_gemm.cu -- FP64 matrix products emulated on the BF16 tensor cores
+// (Ozaki scheme: Ozaki, Ogita, Oishi, Rump, "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication and
+// its applications", Numer. Algorithms 59, 2012).
+//
+//   C (M x N, FP64) = alpha op(A) op(B) + beta C
+//
+// GB300 runs FP64 at ~1.05 TFLOP/s and BF16 at ~1950 TFLOP/s.  Each row r of
+// op(A) is written as 2^{eA_r} sum_{s=1..S} a_s 2^{-7s} with integer digits
+// |a_s| <= 127 (exact in BF16), each column c of op(B) likewise; then
+//   (op(A) op(B))(r,c) = 2^{eA_r + eB_c} sum_d 2^{-7d} sum_{s+t=d} (a_s b_t^T)(r,c).
+// With S = 8 digits (56 bits) and the digit pairs s + t <= S + 1 kept, the
+// error is about K 2^{-56} max|op(A)(r,:)| max|op(B)(:,c)| (digit truncation;
+// the dropped pairs weigh 2^{-70}).  One tcgen05 accumulator per digit sum d
+// lives in TMEM (8 x 64 FP32 columns = all 512); every 128 of K the partial
+// sums are exact integers in FP32 (<= 8 pairs x 128 x 127^2 < 2^24), and they
+// are folded into double-float (hi, lo) FP32 registers with exact
+// power-of-two weights.  The final value gets one FP64 epilogue per element.
+//
+// Splitting works on the FP64 bit pattern with integer instructions only
+// (GB300's FP64 pipe would make a floating-point split cost more than the
+// product): significand m (53 bits), exponent E; the row scale eA_r is the
+// largest E+1 of the row; the digits are the top 7S bits of m aligned to it.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "trace.h"
+
+namespace rutv {
+
+namespace {
+
+constexpr int OZ_S = 8;         // digits per operand
+constexpr int OZ_TM = 128;      // output rows per CTA (UMMA M)
+constexpr int OZ_TN = 64;       // output columns per CTA (UMMA N)
+constexpr int OZ_TK = 64;       // K per stage (128 bytes of BF16)
+constexpr int OZ_CHUNK = 2;     // k-blocks per exact FP32 chunk (K = 128)
+constexpr int OZ_THREADS = 192; // warps 0-3 drain TMEM, warp 4 = TMA, warp 5 = MMA
+constexpr long long kOzWait = 1LL << 24;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
+    const uint32_t a = su32(b);
+    for (long long i = 0; i < kOzWait; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (i > 64) __nanosleep(32);
+    }
+    return false;
+}
+__device__ __forceinline__ void tma2d(void* dst, const CUtensorMap* m, uint64_t* b, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            su32(dst)),
+        "l"((uint64_t)m), "r"(su32(b)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// ---------------------------------------------------------------- splitting
+// Exponent E+1 of a nonzero finite double (|x| < 2^{E+1}); 0-exponent values
+// (zero, subnormal) give INT_MIN so they never set the row scale.
+__device__ __forceinline__ int exp_of(double x) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int be = (int)((bits >> 52) & 0x7FF);
+    return be == 0 ? INT_MIN : be - 1022;
+}
+
+// row maxima of the exponent: L(r, k) = trans ? X(k, r) : X(r, k)
+__global__ void k_oz_rowexp(const double* __restrict__ X, int64_t ld, int R, int K, bool trans, int* __restrict__ e,
+                            int* status) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (trans) {  // row r = column r of X: contiguous, one warp per row
+        for (int r = blockIdx.x * 8 + warp; r < R; r += gridDim.x * 8) {
+            int m = INT_MIN;
+            bool bad = false;
+            for (int k = lane; k < K; k += 32) {
+                double v = X[k + (int64_t)r * ld];
+                bad |= !isfinite(v);
+                m = max(m, exp_of(v));
+            }
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE);
+            if (lane == 0) e[r] = m;
+        }
+    } else {  // row r strided: 32 rows per block, lanes over rows, warps over k
+        __shared__ int sm[8][33];
+        const int r0 = blockIdx.x * 32;
+        const int r = r0 + lane;
+        int m = INT_MIN;
+        bool bad = false;
+        if (r < R)
+            for (int k = warp; k < K; k += 8) {
+                double v = X[r + (int64_t)k * ld];
+                bad |= !isfinite(v);
+                m = max(m, exp_of(v));
+            }
+        if (bad) atomicOr(status, ST_NONFINITE);
+        sm[warp][lane] = m;
+        __syncthreads();
+        if (warp == 0 && r < R) {
+            int mm = sm[0][lane];
+            for (int w = 1; w < 8; ++w) mm = max(mm, sm[w][lane]);
+            e[r] = mm;
+        }
+    }
+}
+
+// digits: Q[s][r][k] (s < OZ_S, row stride ldq, slice stride R*ldq) in BF16
+__device__ __forceinline__ void split_one(double x, int er, uint16_t* out, size_t slice_stride) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int be = (int)((bits >> 52) & 0x7FF);
+    unsigned long long F = 0ull;
+    if (be != 0 && er != INT_MIN) {
+        const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        // |x| / 2^er = mant 2^{be - 1075 - er}; F = floor(that 2^{7S})
+        const int sh = be - 1075 - er + 7 * OZ_S;
+        if (sh >= 0) F = mant << sh;  // F < 2^{7S} <= 2^56 since |x| < 2^er
+        else if (sh > -64) F = mant >> (-sh);
+    }
+    const bool neg = (bits >> 63) != 0;
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+        int digit = (int)((F >> (7 * (OZ_S - 1 - s))) & 127ull);
+        float f = (float)(neg ? -digit : digit);
+        __nv_bfloat16 h = __float2bfloat16_rn(f);
+        out[(size_t)s * slice_stride] = *reinterpret_cast<uint16_t*>(&h);
+    }
+}
+
+__global__ void k_oz_split(const double* __restrict__ X, int64_t ld, int R, int K, bool trans,
+                           const int* __restrict__ e, uint16_t* __restrict__ Q, int64_t ldq) {
+    const size_t slice = (size_t)R * ldq;
+    if (trans) {  // L(r, k) = X(k, r): k contiguous in memory and in Q
+        const int64_t total = (int64_t)R * K;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+            const int k = (int)(i % K), r = (int)(i / K);
+            split_one(X[k + (int64_t)r * ld], e[r], Q + (size_t)r * ldq + k, slice);
+        }
+    } else {  // L(r, k) = X(r, k): transpose through a 32 x 32 tile
+        __shared__ double tile[32][33];
+        const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+        for (int j = ty; j < 32; j += 8) {
+            int r = r0 + tx, k = k0 + j;
+            tile[j][tx] = (r < R && k < K) ? X[r + (int64_t)k * ld] : 0.0;
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            int r = r0 + j, k = k0 + tx;
+            if (r < R && k < K) split_one(tile[tx][j], e[r], Q + (size_t)r * ldq + k, slice);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- product
+struct OzSmem {
+    static constexpr int A_BYTES = OZ_TM * OZ_TK * 2;           // 16 KB
+    static constexpr int B_BYTES = OZ_TN * OZ_TK * 2;           // 8 KB
+    static constexpr int B_SET = OZ_S * B_BYTES;                // 56 KB
+    static constexpr int TOTAL = 2 * A_BYTES + 2 * B_SET + 1024 + 256;
+};
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapB, int M, int N,
+                                                           int K, const int* __restrict__ eA,
+                                                           const int* __restrict__ eB, double alpha, double beta,
+                                                           double* __restrict__ C, int64_t ldc, int* status) {
+    extern __shared__ __align__(1024) uint8_t oz_raw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)oz_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* Abuf = sm;                                   // 2 x A_BYTES
+    uint8_t* Bbuf = sm + 2 * OzSmem::A_BYTES;             // 2 x B_SET
+    uint64_t* bars = (uint64_t*)(sm + 2 * OzSmem::A_BYTES + 2 * OzSmem::B_SET);
+    uint64_t* a_full = bars;       // [2]
+    uint64_t* a_empty = bars + 2;  // [2]
+    uint64_t* b_full = bars + 4;   // [2]
+    uint64_t* b_empty = bars + 6;  // [2]
+    uint64_t* c_full = bars + 8;   // chunk accumulated
+    uint64_t* c_free = bars + 9;   // chunk drained
+    uint32_t* tslot = (uint32_t*)(bars + 10);
+    __shared__ volatile int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * OZ_TM, n0 = blockIdx.y * OZ_TN;
+    const int nkb = (K + OZ_TK - 1) / OZ_TK;
+    const int nchunks = (nkb + OZ_CHUNK - 1) / OZ_CHUNK;
+
+    if (tid == 0) {
+        s_abort = 0;
+        for (int i = 0; i < 2; ++i) {
+            bar_init(&a_full[i], 1);
+            bar_init(&a_empty[i], 1);
+            bar_init(&b_full[i], 1);
+            bar_init(&b_empty[i], 1);
+        }
+        bar_init(c_full, 1);
+        bar_init(c_free, 128);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (warp == 4) {
+        if (lane == 0 && nkb > 0) {  // ---------------- TMA producer
+            int ia = 0, kb_done = 0;
+            for (int kb = 0; kb < nkb && !s_abort; ++kb) {
+                kb_done = kb + 1;
+                const int sb = kb & 1;
+                if (!bar_wait(&b_empty[sb], (uint32_t)(((kb >> 1) & 1) ^ 1))) { s_abort = 1; break; }
+                bar_expect(&b_full[sb], (uint32_t)OzSmem::B_SET);
+                for (int t = 0; t < OZ_S; ++t)
+                    tma2d(Bbuf + sb * OzSmem::B_SET + t * OzSmem::B_BYTES, &mapB, &b_full[sb], kb * OZ_TK,
+                          t * N + n0);
+                for (int s = 0; s < OZ_S; ++s, ++ia) {
+                    const int sa = ia & 1;
+                    if (!bar_wait(&a_empty[sa], (uint32_t)(((ia >> 1) & 1) ^ 1))) { s_abort = 1; break; }
+                    bar_expect(&a_full[sa], (uint32_t)OzSmem::A_BYTES);
+                    tma2d(Abuf + sa * OzSmem::A_BYTES, &mapA, &a_full[sa], kb * OZ_TK, s * M + m0);
+                }
+            }
+            // every copy issued must land before the CTA can exit
+            for (int kb = max(0, kb_done - 2); kb < kb_done; ++kb) bar_wait(&b_full[kb & 1], (uint32_t)((kb >> 1) & 1));
+            for (int i = max(0, ia - 2); i < ia; ++i) bar_wait(&a_full[i & 1], (uint32_t)((i >> 1) & 1));
+        }
+    } else if (warp == 5) {
+        if (lane == 0 && nkb > 0) {  // ---------------- MMA issuer
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) |
+                                   ((uint32_t)(OZ_TM >> 4) << 24);
+            int ia = 0, chunk = 0;
+            for (int kb = 0; kb < nkb && !s_abort; ++kb) {
+                const int sb = kb & 1;
+                const bool first_of_chunk = (kb % OZ_CHUNK) == 0;
+                if (first_of_chunk && chunk > 0) {
+                    if (!bar_wait(c_free, (uint32_t)((chunk - 1) & 1))) { s_abort = 1; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                }
+                if (!bar_wait(&b_full[sb], (uint32_t)((kb >> 1) & 1))) { s_abort = 1; break; }
+                for (int s = 0; s < OZ_S; ++s, ++ia) {
+                    const int sa = ia & 1;
+                    if (!bar_wait(&a_full[sa], (uint32_t)((ia >> 1) & 1))) { s_abort = 1; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t da = desc_sw128(su32(Abuf + sa * OzSmem::A_BYTES));
+                    for (int t = 0; t + s < OZ_S; ++t) {
+                        const uint64_t db = desc_sw128(su32(Bbuf + sb * OzSmem::B_SET + t * OzSmem::B_BYTES));
+                        const uint32_t dt = tmem + (uint32_t)((s + t) * OZ_TN);
+#pragma unroll
+                        for (int k = 0; k < OZ_TK / 16; ++k) {
+                            const uint64_t ko = (uint64_t)((k * 32) >> 4);
+                            const uint32_t acc = (!first_of_chunk || s > 0 || k > 0) ? 1u : 0u;
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
+                                "l"(da + ko), "l"(db + ko), "r"(idesc), "r"(acc)
+                                : "memory");
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     su32(&a_empty[sa]))
+                                 : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(&b_empty[sb]))
+                             : "memory");
+                if ((kb % OZ_CHUNK) == OZ_CHUNK - 1 || kb == nkb - 1) {
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     su32(c_full))
+                                 : "memory");
+                    ++chunk;
+                }
+            }
+        }
+    } else {  // ---------------- warps 0-3: drain TMEM into double-float
+        float hi[OZ_TN], lo[OZ_TN];
+#pragma unroll
+        for (int j = 0; j < OZ_TN; ++j) hi[j] = lo[j] = 0.0f;
+        bool ok = true;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            ok = __all_sync(0xffffffffu, bar_wait(c_full, (uint32_t)(ch & 1)));
+            if (!ok || s_abort) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+            for (int d = OZ_S - 1; d >= 0; --d) {
+                const float w = __int_as_float((127 - 7 * (d + 2)) << 23);  // 2^{-7(d+2)}
+#pragma unroll
+                for (int c0 = 0; c0 < OZ_TN; c0 += 32) {
+                    uint32_t v[32];
+                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * OZ_TN + c0);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                          "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                          "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                        : "r"(ta));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        float s, e;
+                        two_sum(hi[c0 + j], __uint_as_float(v[j]) * w, s, e);
+                        hi[c0 + j] = s;
+                        lo[c0 + j] += e;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < OZ_TN; ++j) {  // renormalise (fast two-sum)
+                float s = hi[j] + lo[j];
+                lo[j] = lo[j] - (s - hi[j]);
+                hi[j] = s;
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            bar_arrive(c_free);
+        }
+        if (!ok && lane == 0) atomicOr(status, ST_TIMEOUT);
+        const int r = m0 + warp * 32 + lane;
+        if (ok && !s_abort && r < M) {
+            const int er = eA[r];
+#pragma unroll
+            for (int j = 0; j < OZ_TN; ++j) {
+                const int c = n0 + j;
+                if (c >= N) break;
+                double* cp = C + r + (int64_t)c * ldc;
+                const int ec = eB[c];
+                double v = 0.0;
+                if (er != INT_MIN && ec != INT_MIN) {
+                    // 2^{er+ec} built from its bits (|er + ec| stays far inside the normal range)
+                    const double scale = __longlong_as_double((long long)(er + ec + 1023) << 52) * alpha;
+                    v = fma((double)hi[j], scale, (double)lo[j] * scale);
+                }
+                *cp = (beta == 0.0) ? v : fma(beta, *cp, v);
+            }
+        }
+    }
+    if (s_abort && tid == 0) atomicOr(status, ST_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 oz_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+bool oz_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+    auto enc = oz_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)OZ_TK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+unsigned oz_grid(int64_t total) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 8192)); }
+
+}  // namespace
+
+int64_t oz_ldq(int64_t K) { return (K + 63) / 64 * 64; }
+
+size_t oz_work_bytes(int64_t M, int64_t N, int64_t K) {
+    const int64_t ldq = oz_ldq(K);
+    return (size_t)OZ_S * 2 * ((size_t)M * ldq + (size_t)N * ldq) + 4 * (size_t)(M + N) + 1024;
+}
+
+cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+                    const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work, int* status,
+                    cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (M < OZ_TM || N < OZ_TN || K < OZ_TK) return cudaErrorInvalidValue;  // one TMA box at least
+    const int64_t ldq = oz_ldq(K);
+    uint16_t* QA = (uint16_t*)work;
+    uint16_t* QB = QA + (size_t)OZ_S * M * ldq;
+    int* eA = (int*)(QB + (size_t)OZ_S * N * ldq);
+    int* eB = eA + M;
+    // op(A) (M x K): row r = trans ? column r of A : row r of A
+    // op(B) (K x N) viewed as N x K K-major: row c = tb ? row c of B... : column c of B
+    const bool a_rows_contig = ta;   // op(A)(r,k) = A(k,r)
+    const bool b_rows_contig = !tb;  // Bk(c,k) = op(B)(k,c) = B(k,c)  (tb: B(c,k))
+    if (a_rows_contig)
+        k_oz_rowexp<<<(unsigned)std::min<int64_t>(cdiv(M, 8), 4096), 256, 0, st>>>(A, lda, (int)M, (int)K, true, eA,
+                                                                                      status);
+    else
+        k_oz_rowexp<<<(unsigned)cdiv(M, 32), 256, 0, st>>>(A, lda, (int)M, (int)K, false, eA, status);
+    if (b_rows_contig)
+        k_oz_rowexp<<<(unsigned)std::min<int64_t>(cdiv(N, 8), 4096), 256, 0, st>>>(B, ldb, (int)N, (int)K, true, eB,
+                                                                                      status);
+    else
+        k_oz_rowexp<<<(unsigned)cdiv(N, 32), 256, 0, st>>>(B, ldb, (int)N, (int)K, false, eB, status);
+    if (a_rows_contig)
+        k_oz_split<<<oz_grid(M * K), 256, 0, st>>>(A, lda, (int)M, (int)K, true, eA, QA, ldq);
+    else
+        k_oz_split<<<dim3((unsigned)cdiv(M, 32), (unsigned)cdiv(K, 32)), 256, 0, st>>>(A, lda, (int)M, (int)K, false,
+                                                                                        eA, QA, ldq);
+    if (b_rows_contig)
+        k_oz_split<<<oz_grid(N * K), 256, 0, st>>>(B, ldb, (int)N, (int)K, true, eB, QB, ldq);
+    else
+        k_oz_split<<<dim3((unsigned)cdiv(N, 32), (unsigned)cdiv(K, 32)), 256, 0, st>>>(B, ldb, (int)N, (int)K, false,
+                                                                                        eB, QB, ldq);
+    trace_count(4);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    CUtensorMap ma, mb;
+    if (!oz_map(&ma, QA, (int64_t)OZ_S * M, K, ldq, OZ_TM)) return cudaErrorInvalidValue;
+    if (!oz_map(&mb, QB, (int64_t)OZ_S * N, K, ldq, OZ_TN)) return cudaErrorInvalidValue;
+    static bool configured = false;
+    if (!configured) {
+        e = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OzSmem::TOTAL);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((unsigned)cdiv(M, OZ_TM), (unsigned)cdiv(N, OZ_TN));
+    k_oz_gemm<<<grid, OZ_THREADS, OzSmem::TOTAL, st>>>(ma, mb, (int)M, (int)N, (int)K, eA, eB, alpha, beta, C, ldc,
+                                                       status);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+}  // namespace rutv

@@ -52,9 +52,10 @@ struct Workspace {
     int* qdev;        // chosen q
     double* dq;       // candidate diagonals, 4 x w (trace mode)
     float* qmodel;    // network parameters on the device
+    void* oz;         // digit slices and exponents of the emulated FP64 products
 };
 
-constexpr int kSlots = 28;
+constexpr int kSlots = 29;
 struct Layout {
     size_t off[kSlots];
     size_t total;
@@ -63,7 +64,11 @@ struct Layout {
 
 int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
-bool lowp_prec(int prec) { return prec == RANDUTV_SKETCH_BF16 || prec == RANDUTV_SKETCH_FP16_SCALED; }
+bool lowp_prec(int prec) {
+    return prec == RANDUTV_SKETCH_BF16 || prec == RANDUTV_SKETCH_FP16_SCALED || prec == RANDUTV_EMULATED_SKETCH_BF16;
+}
+bool emulated_prec(int prec) { return prec == RANDUTV_FP64_EMULATED || prec == RANDUTV_EMULATED_SKETCH_BF16; }
+bool valid_prec(int prec) { return prec == RANDUTV_FP64 || lowp_prec(prec) || emulated_prec(prec); }
 
 int device_sms(int dev) {
     static std::mutex mu;
@@ -113,7 +118,8 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec) {
         lp ? sizeof(float) * cholqr_scratch_floats((int)npad, sms) : 0,
         lp ? sizeof(unsigned long long) : 0,                        // max |T22|
         sizeof(float) * 32 + sizeof(double) * 4 * (size_t)wmax,     // learned-q features, q, candidates
-        sizeof(float) * (size_t)learnq_nparam()};                   // learned-q model
+        sizeof(float) * (size_t)learnq_nparam(),                    // learned-q model
+        emulated_prec(prec) ? oz_work_bytes(mx, std::max<int64_t>(wmax, 128), mx) : 0};  // Ozaki digits
     size_t o = 0;
     for (int i = 0; i < kSlots; ++i) {
         L.off[i] = o;
@@ -158,6 +164,7 @@ Workspace carve(void* base, const Layout& L) {
     w.qdev = (int*)(w.feat + 16);
     w.dq = (double*)(p + L.off[26] + sizeof(float) * 32);
     w.qmodel = (float*)(p + L.off[27]);
+    w.oz = (void*)(p + L.off[28]);
     return w;
 }
 
@@ -220,6 +227,8 @@ cudaError_t gemm(Ctx& c, const char* role, bool ta, bool tb, int64_t M, int64_t 
     double flops = 2.0 * (double)M * (double)N * (double)K;
     double bytes = 8.0 * ((double)M * K + (double)K * N + (double)M * N * (beta != 0.0 ? 2.0 : 1.0));
     TraceScope ts(role, flops, bytes, c.st);
+    if (emulated_prec(c.prec) && M >= 128 && N >= 64 && K >= 64)
+        return oz_gemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.w.oz, c.w.status, c.st);
     return gemm_f64(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.w.part, c.w.part_elems, c.sms, c.st);
 }
 
@@ -542,7 +551,7 @@ const char* randutv_status_string(int s) {
 
 size_t randutv_workspace_size(int64_t m, int64_t n, int b, int prec) {
     if (m < n || n < 0 || b < 1) return 0;
-    if (prec != RANDUTV_FP64 && !lowp_prec(prec)) return 0;
+    if (!valid_prec(prec)) return 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
     return make_layout(m, n, b, device_sms(dev), prec).total;
@@ -568,7 +577,7 @@ randutv_status factor_impl(int64_t m, int64_t n, const double* A, int64_t lda, i
                            double* T, double* V, int prec, void* stream, void* workspace, size_t ws_bytes,
                            int64_t stop_after, int* info, const ModeArgs& ma) {
     if (!args_ok(m, n, A, lda, b, q, T)) return RANDUTV_EINVAL;
-    if (prec != RANDUTV_FP64 && !lowp_prec(prec)) return RANDUTV_ENOTIMPL;
+    if (!valid_prec(prec)) return RANDUTV_ENOTIMPL;
     if (A == T && lda != m) return RANDUTV_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;

@@ -200,11 +200,11 @@ __global__ void __launch_bounds__(256) k_chol32(const float* __restrict__ Gp, in
         }
         __syncthreads();
         const float piv = s_piv, inv = 1.0f / piv;
-        const int rem = b - j - 1;
-        // trailing update with the scaled row computed on the fly
-        for (int e = tid; e < rem * rem; e += nt) {
-            int p = j + 1 + e % rem, c = j + 1 + e / rem;
-            if (p <= c) G[p + (size_t)c * b] -= (G[j + (size_t)p * b] * inv) * (G[j + (size_t)c * b] * inv);
+        // trailing update, one column per thread (row j scaled on the fly)
+        for (int c = j + 1 + tid; c < b; c += nt) {
+            float* gc = G + (size_t)c * b;
+            const float rc = gc[j] * inv;
+            for (int p = j + 1; p <= c; ++p) gc[p] -= (G[j + (size_t)p * b] * inv) * rc;
         }
         __syncthreads();
         for (int c = j + 1 + tid; c < b; c += nt) G[j + (size_t)c * b] *= inv;
@@ -311,10 +311,19 @@ cudaError_t cholqr32(float* X, int64_t L, int b, int passes, uint16_t* Xb, int64
         configured = true;
     }
     for (int p = 0; p < passes; ++p) {
-        k_gram32<<<parts, 256, shm_gram, st>>>(X, (int)L, b, chunk, Gp);
-        k_chol32<<<1, 256, shm_chol, st>>>(Gp, parts, b, (int)L, p == 0 ? 1 : 0, G, R, small);
-        k_trsm32<<<(unsigned)cdiv(L, 128), 128, shm_trsm, st>>>(X, (int)L, b, R, p == passes - 1 ? Xb : nullptr,
-                                                                  ldb, f16, small);
+        {
+            TraceScope ts("cholqr_gram", 2.0 * (double)L * b * b, 4.0 * (double)L * b, st);
+            k_gram32<<<parts, 256, shm_gram, st>>>(X, (int)L, b, chunk, Gp);
+        }
+        {
+            TraceScope ts("cholqr_chol", (double)b * b * b / 3.0, 4.0 * (double)parts * b * b, st);
+            k_chol32<<<1, 256, shm_chol, st>>>(Gp, parts, b, (int)L, p == 0 ? 1 : 0, G, R, small);
+        }
+        {
+            TraceScope ts("cholqr_trsm", (double)L * b * b, 8.0 * (double)L * b, st);
+            k_trsm32<<<(unsigned)cdiv(L, 128), 128, shm_trsm, st>>>(X, (int)L, b, R, p == passes - 1 ? Xb : nullptr,
+                                                                      ldb, f16, small);
+        }
         trace_count(3);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
