@@ -3,12 +3,16 @@
 One step = one complete factorization A = U T V^T (every block step: sketch,
 QR of the sketch, right WY update, panel QR, left WY update, b x b SVD) of a
 16000 x 16000 FP64 matrix with the gap spectrum, b = 128, q = 2, U and V formed.
+The default path computes every FP64 product emulated on the BF16 tensor
+cores (RANDUTV_FP64_EMULATED); one plain-FP64 (DMMA) factorization of the same
+matrix is timed beside it for the ratio (`vs_plain_fp64`).
 value = whole-job effective TFLOP/s from the fixed randUTV flop count F (below),
 summed over ranks (one independent factorization per GPU: replicas, weak
 scaling).  Prints ONE JSON line on rank 0.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--n 16000] [--b 128] [--q 2] [--prec fp64|bf16] [--no-e2e] [--no-cpu]
+                    [--n 16000] [--b 128] [--q 2] [--prec emul|emul_bf16|fp64|bf16|fp16]
+                    [--workload single|batched] [--no-e2e] [--no-cpu] [--no-compare]
 
 --impl reference times the CPU oracle (the plain FP64 randUTV used as the
 parity reference) on the host cores, each step a bounded sample of the same
@@ -30,6 +34,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "randUTV s/factorization & TFLOP/s at n=16000: mixed/learned-q vs FP64, % peak"
+# digit products per emulated FP64 product (8 digits, pairs s + t <= 9)
+OZ_PAIRS = 36
+DTYPES = {"fp64": "f64", "bf16": "f64+bf16-sketch", "fp16": "f64+fp16-sketch",
+          "emul": "f64 (products emulated on bf16 tensor cores)",
+          "emul_bf16": "f64 (products emulated on bf16 tensor cores)+bf16-sketch"}
+
+
+def measured_peak(key: str, fallback: float) -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError):
+        return fallback
+
+
 # ncu: 222.2 MB of DRAM traffic for the 4.295 GFLOP rank-128 update launch (4096^2)
 GEMM_F64_DRAM_BYTES_PER_FLOP = 222.2e6 / (2.0 * 4096 * 4096 * 128)
 
@@ -205,7 +224,8 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    m = n = args.n
+    n = args.n
+    m = args.m if args.m > 0 else n
     b, q = args.b, args.q
     prec = {"fp64": rutv.RANDUTV_FP64, "bf16": rutv.RANDUTV_SKETCH_BF16,
             "fp16": rutv.RANDUTV_SKETCH_FP16_SCALED, "emul": rutv.RANDUTV_FP64_EMULATED,
@@ -222,10 +242,17 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    qnet = rutv.load_qnet() if args.learnedq else None
+    q_used = []
+
     def step():
-        st = rutv.randutv_factor_ex(m, n, A, m, b, q, 0, U, T, V, prec, stream, ws, ws_bytes, -1, None)
+        if args.learnedq:
+            st, qu = rutv.randutv_factor_learnedq(m, n, A, m, b, qnet, 0, U, T, V, prec=prec, stream=stream)
+            q_used[:] = qu
+        else:
+            st = rutv.randutv_factor_ex(m, n, A, m, b, q, 0, U, T, V, prec, stream, ws, ws_bytes, -1, None)
         if st != rutv.RANDUTV_OK:
-            raise rutv.RandUTVError(st, "randutv_factor_ex")
+            raise rutv.RandUTVError(st, "randutv_factor")
 
     for _ in range(args.warmup):
         step()
@@ -269,29 +296,102 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
         quality = {"Tii_over_sigma_median": float(np.median(r)), "Tii_over_sigma_first_block_max_dev":
                    float(np.abs(r[:b] - 1).max())}
 
-    # dominant kernel: the FP64 DMMA GEMM (all its launches, with their split-K reduce)
+    # dominant kernel: the FP64 products (class names "gemm_*"), all their launches
     g_ms = sum(v["ms"] for k, v in trace.items() if k.startswith("gemm"))
     g_fl = sum(v["flops"] for k, v in trace.items() if k.startswith("gemm"))
     g_launch = sum(v["scopes"] for k, v in trace.items() if k.startswith("gemm"))
     tot_ms = sum(v["ms"] for v in trace.values())
-    achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None
-    roofline = {
-        "kernel": "k_gemm_f64 (FP64 mma.sync m8n8k4, with its split-K reduce)",
-        "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-        "frac": (achieved / fp64_peak) if achieved else None,
-        # DRAM bytes per flop of one ncu-captured launch of this kernel (the
-        # 4096^2 rank-128 update, profiles/gemm_f64_rank128_4096.md) times the
-        # average flops of a launch here
-        "traffic": GEMM_F64_DRAM_BYTES_PER_FLOP * g_fl / max(g_launch, 1),
-        "traffic_source": "ncu dram__bytes_read+write of k_gemm_f64 on the 4096^2 case (0.0518 B/flop), "
-                          "scaled by the average flops per launch",
-        "peak_source": "cuBLAS DGEMM 8192^3 measured in this run (MEASURED_PEAKS.json has no FP64 entry)",
-        "launches": g_launch, "share_of_traced_time": g_ms / tot_ms if tot_ms else None,
-        "avg_flops_per_launch": g_fl / max(g_launch, 1),
-        "avg_ms_per_launch": g_ms / max(g_launch, 1),
-    }
+    if args.prec in ("emul", "emul_bf16"):
+        # k_oz_gemm executes OZ_PAIRS BF16 digit products per FP64 product
+        # (plus its digit split); its roofline is that BF16 tensor work against
+        # the measured BF16 peak
+        bf_fl = OZ_PAIRS * g_fl
+        achieved = bf_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None
+        bf16_peak = measured_peak("bf16_tflops", 1917.9)
+        roofline = {
+            "kernel": "k_oz_gemm (FP64 product emulated by %d BF16 digit products on tcgen05, "
+                      "with its digit split)" % OZ_PAIRS,
+            "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": (achieved / bf16_peak) if achieved else None, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
+            "fp64_equivalent_tflops": g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None,
+            "launches": g_launch, "share_of_traced_time": g_ms / tot_ms if tot_ms else None,
+            "avg_flops_per_launch": bf_fl / max(g_launch, 1), "avg_ms_per_launch": g_ms / max(g_launch, 1),
+        }
+    else:
+        achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None
+        roofline = {
+            "kernel": "k_gemm_f64 (FP64 mma.sync m8n8k4, with its split-K reduce)",
+            "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": (achieved / fp64_peak) if achieved else None,
+            # DRAM bytes per flop of one ncu-captured launch of this kernel (the
+            # 4096^2 rank-128 update, profiles/gemm_f64_rank128_4096.md) times the
+            # average flops of a launch here
+            "traffic": GEMM_F64_DRAM_BYTES_PER_FLOP * g_fl / max(g_launch, 1),
+            "traffic_source": "ncu dram__bytes_read+write of k_gemm_f64 on the 4096^2 case (0.0518 B/flop), "
+                              "scaled by the average flops per launch",
+            "peak_source": "cuBLAS DGEMM 8192^3 measured in this run (MEASURED_PEAKS.json has no FP64 entry)",
+            "launches": g_launch, "share_of_traced_time": g_ms / tot_ms if tot_ms else None,
+            "avg_flops_per_launch": g_fl / max(g_launch, 1),
+            "avg_ms_per_launch": g_ms / max(g_launch, 1),
+        }
     breakdown = {k: {"ms": round(v["ms"] / args.steps, 3), "launches": v["kernels"] // args.steps}
                  for k, v in sorted(trace.items(), key=lambda kv: -kv[1]["ms"])}
+
+    # quality against a reference precision (same matrix, same seed)
+    ref_quality = None
+    if args.ref_prec or args.learnedq:
+        import numpy as np
+        rp = {"": prec, "fp64": rutv.RANDUTV_FP64, "emul": rutv.RANDUTV_FP64_EMULATED}[args.ref_prec]
+        d_run = torch.diagonal(T).abs().cpu().numpy()
+        wsr_bytes = rutv.randutv_workspace_size(m, n, b, rp)
+        wsr = torch.empty(max(wsr_bytes, 1), dtype=torch.uint8, device=dev)
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        r0.record(stream)
+        st = rutv.randutv_factor_ex(m, n, A, m, b, q, 0, U, T, V, rp, stream, wsr, wsr_bytes, -1, None)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        if st != rutv.RANDUTV_OK:
+            raise rutv.RandUTVError(st, "randutv_factor_ex (reference)")
+        d_ref = torch.diagonal(T).abs().cpu().numpy()
+        del wsr
+        keep = (sigma > 1e3 * 2.0 ** -53 * sigma[0]) if sigma is not None else (d_ref > 1e3 * 2.0 ** -53 * d_ref[0])
+        sg = sigma if sigma is not None else d_ref
+        r_run, r_ref = d_run[keep] / sg[keep], d_ref[keep] / sg[keep]
+        dev_ = np.abs(r_run / r_ref - 1.0)
+        ok = (dev_ <= 0.05) | (np.abs(np.log(r_run)) <= np.abs(np.log(r_ref)))
+        ref_quality = {"reference": ("fixed q=%d, " % q if args.learnedq else "") +
+                       {"": args.prec, "fp64": "fp64", "emul": "emul"}[args.ref_prec],
+                       "reference_s_per_factorization": r0.elapsed_time(r1) / 1e3,
+                       "Tii_ratio_max_dev": float(dev_.max()), "Tii_ratio_median_dev": float(np.median(dev_)),
+                       "frac_within_5pct_or_better": float(ok.mean())}
+        if args.learnedq:
+            ref_quality["q_used"] = [int(x) for x in q_used]
+            ref_quality["power_iterations"] = int(sum(x for x in q_used if x >= 0))
+            ref_quality["power_iterations_fixed_q"] = int(q * sum(1 for x in q_used if x >= 0))
+
+    # the plain FP64 path (DMMA products) on the same matrix, once, for the time ratio
+    compare = None
+    if not args.no_compare and args.prec != "fp64":
+        ws64_bytes = rutv.randutv_workspace_size(m, n, b, rutv.RANDUTV_FP64)
+        ws64 = torch.empty(max(ws64_bytes, 1), dtype=torch.uint8, device=dev)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        c0.record(stream)
+        st = rutv.randutv_factor_ex(m, n, A, m, b, q, 0, U, T, V, rutv.RANDUTV_FP64, stream, ws64, ws64_bytes, -1,
+                                    None)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        if st != rutv.RANDUTV_OK:
+            raise rutv.RandUTVError(st, "randutv_factor_ex (FP64)")
+        t64 = c0.elapsed_time(c1) / 1e3
+        compare = {"path": "plain FP64 (DMMA products), same matrix, one timed run after the primary runs",
+                   "s_per_factorization": t64, "tflops": F / t64 / 1e12,
+                   "speedup_of_primary": t64 / (ms_per_step / 1e3)}
+        del ws64
 
     # end to end through the C ABI on HOST buffers (copies inside the timed region)
     e2e = None
@@ -330,15 +430,18 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "s_per_factorization": ms_per_step / 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.prec == "fp64" else "f64+%s-sketch" % args.prec, "data": "synthetic",
-            "config": {"workload": "randUTV %s %dx%d, %s spectrum, b=%d, q=%d, U and V formed" %
-                       (args.prec.upper(), m, n, args.spectrum, b, q),
+            "dtype": DTYPES[args.prec], "data": "synthetic",
+            "config": {"workload": "randUTV %s %dx%d, %s spectrum, b=%d, %s, U and V formed" %
+                       (args.prec.upper(), m, n, args.spectrum, b,
+                        "learned q (fallback q=%d)" % q if args.learnedq else "q=%d" % q),
                        "m": m, "n": n, "b": b, "q": q, "spectrum": args.spectrum, "precision": args.prec,
                        "flops_per_factorization": F,
                        "l2": "inputs larger than L2 (A, T, U, V are 2.05 GB each)",
                        "parallelism": "replicas x%d" % world},
             "fp64_peak_tflops": fp64_peak,
             "pct_of_fp64_peak": 100.0 * (value / world) / fp64_peak,
+            "vs_plain_fp64": compare,
+            "quality_vs_reference": ref_quality,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -395,7 +498,8 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         U.append(rutv.colmajor_empty(ms[j], ms[j], dev))
         V.append(rutv.colmajor_empty(ns[j], ns[j], dev))
     seeds = list(mine)
-    prec = {"fp64": rutv.RANDUTV_FP64, "fp32": rutv.RANDUTV_SKETCH_FP32}[args.prec if args.prec != "bf16" else "fp64"]
+    # the batched kernel runs FP64 products (DMMA) or, with --prec fp32, an FP32 sketch
+    prec = rutv.RANDUTV_SKETCH_FP32 if args.prec == "fp32" else rutv.RANDUTV_FP64
     t0 = time.perf_counter()
     r, table = rutv.randutv_batched_autotune(ms, ns, A, ms, U, T, V, seeds, q, prec)
     t_tune = time.perf_counter() - t0
@@ -447,7 +551,7 @@ def run_batched(args, rank: int, world: int, local_rank: int):
             "metric": METRIC, "value": F / (ms_step * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "s_per_batch": ms_step / 1e3,
             "higher_is_better": True, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
-            "dtype": "f64" if args.prec != "fp32" else "f64+fp32-sketch", "data": "synthetic",
+            "dtype": "f64+fp32-sketch" if args.prec == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": "batched randUTV, %d matrices, n log-uniform in [32, 512], 25%% with m = 2n, "
                                    "sigma_i = 10^(-8(i-1)/(n-1)), q=%d, U and V formed" % (args.count, q),
                        "count": args.count, "q": q, "parallelism": "LPT shard over %d ranks" % world, "autotune_table": table, "autotune_seconds": t_tune,
@@ -464,10 +568,16 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=16000)
+    p.add_argument("--m", type=int, default=0, help="rows (default: n, square)")
+    p.add_argument("--ref-prec", default="", choices=["", "fp64", "emul"],
+                   help="also factor with this precision and report T_ii/sigma_i against it")
+    p.add_argument("--learnedq", action="store_true",
+                   help="primary path picks q per block with the shipped network (fixed q=2 timed beside it)")
     p.add_argument("--b", type=int, default=128)
     p.add_argument("--q", type=int, default=2)
     p.add_argument("--spectrum", default="gap")
-    p.add_argument("--prec", default="fp64", choices=["fp64", "bf16", "fp16", "fp32", "emul", "emul_bf16"])
+    p.add_argument("--prec", default="emul", choices=["fp64", "bf16", "fp16", "fp32", "emul", "emul_bf16"])
+    p.add_argument("--no-compare", action="store_true", help="skip the timed plain-FP64 (DMMA) factorization")
     p.add_argument("--workload", default="single", choices=["single", "batched"])
     p.add_argument("--count", type=int, default=4096)
     p.add_argument("--no-e2e", action="store_true")

@@ -29,16 +29,17 @@ cudaError_t panel_qr(double* P, int64_t ld, int64_t len, int w, double* tau, dou
                      unsigned* bar, int* status, int sms, cudaStream_t st);
 // W (len x w, ld len) := unit lower trapezoidal part of the QR storage P.
 cudaError_t extract_w(const double* P, int64_t ld, int64_t len, int w, double* W, cudaStream_t st);
-// Upper triangular Tf (w x w) of Q = I - W Tf W^T from Gram = W^T W and tau.
+// Upper triangular Tf (w x w, ld w) of Q = I - W Tf W^T from Gram = W^T W and tau.
 cudaError_t tfactor(const double* gram, const double* tau, int w, double* Tf, int* status,
                     cudaStream_t st);
 
 // ---- b x b one-sided Jacobi SVD (svd.cu) ------------------------------------
 size_t jacobi_scratch_elems(int w);
 // SVD of the upper triangle of R (w x w, ldr): D (w), Us, Vs (w x w, ld w).
+// allow_cluster = false forces the grid variant that works in `scratch`.
 cudaError_t jacobi_svd(const double* R, int64_t ldr, int w, double* D, double* Us, double* Vs,
                        double* scratch, unsigned* bar, int* counters, int* status, int max_sweeps,
-                       cudaStream_t st);
+                       cudaStream_t st, bool allow_cluster = true);
 
 // ---- element-wise kernels (misc.cu) ---------------------------------------
 cudaError_t gaussian_f64(uint64_t seed, int64_t step, int64_t rows, int64_t cols, double* G, int64_t ldg,
@@ -83,10 +84,11 @@ cudaError_t learnq_predict(const float* P, const float* X, int N, float* probs, 
 // ---- FP64 products emulated on BF16 tensor cores (oz_gemm.cu) ---------------
 int64_t oz_ldq(int64_t K);
 size_t oz_work_bytes(int64_t M, int64_t N, int64_t K);
-// Needs M >= 128, N >= 64, K >= 64; `work` holds oz_work_bytes(M, N, K) bytes.
+// Needs M >= 128, N >= 64, K >= 64; `work` holds oz_work_bytes(M, N, K) bytes
+// (digits, exponents and the FP64 split-K partials).
 cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
-                    const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work, int* status,
-                    cudaStream_t st);
+                    const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work, size_t work_bytes,
+                    int sms, int* status, cudaStream_t st);
 cudaError_t set_eye_rect(double* X, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st);
 
 }  // namespace rutv

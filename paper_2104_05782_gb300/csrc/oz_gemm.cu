@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                                                            const __grid_constant__ CUtensorMap mapB, int M, int N,
                                                            int K, const int* __restrict__ eA,
                                                            const int* __restrict__ eB, double alpha, double beta,
-                                                           double* __restrict__ C, int64_t ldc, int* status) {
+                                                           double* __restrict__ C, int64_t ldc, int kbs,
+                                                           double* __restrict__ P, int* status) {
     extern __shared__ __align__(1024) uint8_t oz_raw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)oz_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* Abuf = sm;                                   // 2 x A_BYTES
@@ -213,8 +214,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * OZ_TM, n0 = blockIdx.y * OZ_TN;
-    const int nkb = (K + OZ_TK - 1) / OZ_TK;
+    // split z covers k-blocks [kb0, kb0 + nkb); gridDim.z > 1 writes FP64 partials to P
+    const int nkb_all = (K + OZ_TK - 1) / OZ_TK;
+    const int kb0 = blockIdx.z * kbs;
+    const int nkb = max(0, min(nkb_all, kb0 + kbs) - kb0);
     const int nchunks = (nkb + OZ_CHUNK - 1) / OZ_CHUNK;
+    const bool partial = gridDim.z > 1;
 
     if (tid == 0) {
         s_abort = 0;
@@ -248,13 +253,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                 if (!bar_wait(&b_empty[sb], (uint32_t)(((kb >> 1) & 1) ^ 1))) { s_abort = 1; break; }
                 bar_expect(&b_full[sb], (uint32_t)OzSmem::B_SET);
                 for (int t = 0; t < OZ_S; ++t)
-                    tma2d(Bbuf + sb * OzSmem::B_SET + t * OzSmem::B_BYTES, &mapB, &b_full[sb], kb * OZ_TK,
+                    tma2d(Bbuf + sb * OzSmem::B_SET + t * OzSmem::B_BYTES, &mapB, &b_full[sb], (kb0 + kb) * OZ_TK,
                           t * N + n0);
                 for (int s = 0; s < OZ_S; ++s, ++ia) {
                     const int sa = ia & 1;
                     if (!bar_wait(&a_empty[sa], (uint32_t)(((ia >> 1) & 1) ^ 1))) { s_abort = 1; break; }
                     bar_expect(&a_full[sa], (uint32_t)OzSmem::A_BYTES);
-                    tma2d(Abuf + sa * OzSmem::A_BYTES, &mapA, &a_full[sa], kb * OZ_TK, s * M + m0);
+                    tma2d(Abuf + sa * OzSmem::A_BYTES, &mapA, &a_full[sa], (kb0 + kb) * OZ_TK, s * M + m0);
                 }
             }
             // every copy issued must land before the CTA can exit
@@ -354,6 +359,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
         }
         if (!ok && lane == 0) atomicOr(status, ST_TIMEOUT);
         const int r = m0 + warp * 32 + lane;
+        double* Pz = partial ? P + (size_t)blockIdx.z * (size_t)M * (size_t)N : nullptr;
         if (ok && !s_abort && r < M) {
             const int er = eA[r];
 #pragma unroll
@@ -368,7 +374,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                     const double scale = __longlong_as_double((long long)(er + ec + 1023) << 52) * alpha;
                     v = fma((double)hi[j], scale, (double)lo[j] * scale);
                 }
-                *cp = (beta == 0.0) ? v : fma(beta, *cp, v);
+                if (partial) Pz[r + (size_t)c * M] = v;
+                else *cp = (beta == 0.0) ? v : fma(beta, *cp, v);
             }
         }
     }
@@ -377,6 +384,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+}
+
+// C = sum_z P[z] (fixed order) + beta C
+__global__ void k_oz_reduce(int M, int N, int S, const double* __restrict__ P, double beta, double* __restrict__ C,
+                            int64_t ldc) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int z = 0; z < S; ++z) s += P[(size_t)z * total + e];
+        double* c = C + (e % M) + (e / M) * ldc;
+        *c = (beta == 0.0) ? s : fma(beta, *c, s);
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 oz_encode() {
@@ -410,14 +429,28 @@ unsigned oz_grid(int64_t total) { return (unsigned)std::max<int64_t>(1, std::min
 
 int64_t oz_ldq(int64_t K) { return (K + 63) / 64 * 64; }
 
+// split-K factor: slices of whole 128-deep chunks until the grid covers the
+// SMs about twice; partials (FP64) need splits * M * N doubles
+int oz_splits(int64_t M, int64_t N, int64_t K, int sms) {
+    const int64_t tiles = cdiv(M, OZ_TM) * cdiv(N, OZ_TN);
+    const int64_t chunks = cdiv(cdiv(K, OZ_TK), OZ_CHUNK);
+    int64_t s = 1;
+    if (tiles < 2LL * sms) s = cdiv(2LL * sms, tiles);
+    if (s > chunks) s = chunks;
+    if (s > 64) s = 64;
+    if ((size_t)s * M * N > ((size_t)1 << 27)) s = 1;  // partials bounded at 1 GiB
+    return (int)std::max<int64_t>(s, 1);
+}
+
 size_t oz_work_bytes(int64_t M, int64_t N, int64_t K) {
     const int64_t ldq = oz_ldq(K);
-    return (size_t)OZ_S * 2 * ((size_t)M * ldq + (size_t)N * ldq) + 4 * (size_t)(M + N) + 1024;
+    return (size_t)OZ_S * 2 * ((size_t)M * ldq + (size_t)N * ldq) + 4 * (size_t)(M + N) + 1024 +
+           sizeof(double) * ((size_t)1 << 27);
 }
 
 cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
-                    const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work, int* status,
-                    cudaStream_t st) {
+                    const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work, size_t work_bytes,
+                    int sms, int* status, cudaStream_t st) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (M < OZ_TM || N < OZ_TN || K < OZ_TK) return cudaErrorInvalidValue;  // one TMA box at least
     const int64_t ldq = oz_ldq(K);
@@ -425,6 +458,10 @@ cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double al
     uint16_t* QB = QA + (size_t)OZ_S * M * ldq;
     int* eA = (int*)(QB + (size_t)OZ_S * N * ldq);
     int* eB = eA + M;
+    double* P = (double*)(((uintptr_t)(eB + N) + 255) & ~(uintptr_t)255);
+    int splits = oz_splits(M, N, K, sms);
+    const size_t used = (size_t)((char*)P - (char*)work);
+    if (used + sizeof(double) * (size_t)splits * M * N > work_bytes) splits = 1;
     // op(A) (M x K): row r = trans ? column r of A : row r of A
     // op(B) (K x N) viewed as N x K K-major: row c = tb ? row c of B... : column c of B
     const bool a_rows_contig = ta;   // op(A)(r,k) = A(k,r)
@@ -461,9 +498,16 @@ cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double al
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid((unsigned)cdiv(M, OZ_TM), (unsigned)cdiv(N, OZ_TN));
+    const int64_t nkb = cdiv(K, OZ_TK);
+    const int kbs = (int)(cdiv(cdiv(nkb, OZ_CHUNK), splits) * OZ_CHUNK);  // whole chunks per split
+    splits = (int)cdiv(nkb, kbs);
+    dim3 grid((unsigned)cdiv(M, OZ_TM), (unsigned)cdiv(N, OZ_TN), (unsigned)splits);
     k_oz_gemm<<<grid, OZ_THREADS, OzSmem::TOTAL, st>>>(ma, mb, (int)M, (int)N, (int)K, eA, eB, alpha, beta, C, ldc,
-                                                       status);
+                                                       kbs, P, status);
+    trace_count(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || splits == 1) return e;
+    k_oz_reduce<<<oz_grid(M * N), 256, 0, st>>>((int)M, (int)N, splits, P, beta, C, ldc);
     trace_count(1);
     return cudaGetLastError();
 }

@@ -32,6 +32,10 @@ namespace {
 constexpr int PNT = 256;          // threads per block of the panel kernel
 constexpr int kMaxChunk = 4096;   // rows per block (shared-memory bound)
 
+// SLAB = true keeps the block's rows [r0, r0 + chunk) of the panel in shared
+// memory for the whole factorization (one load, one store); false works on
+// the panel in global memory (for slabs that do not fit).
+template <bool SLAB>
 __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_t ld, int len, int w,
                                                   double* __restrict__ tau, double* __restrict__ part,
                                                   double* __restrict__ piv, unsigned* bar, int* status,
@@ -41,6 +45,7 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
     double* xsb1 = smem + chunk;
     double* sred = smem + 2 * chunk;
     double* wv = sred + w;
+    double* slab = wv + w;  // chunk x w, column-major (SLAB only)
     __shared__ double s_scalars[4];
 
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -49,24 +54,33 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
     const int r1 = min(len, r0 + chunk);
     const int nr = max(0, r1 - r0);
     unsigned target = 0;
+    // entry (r0 + t, c) of the panel, t < nr: own rows only
+    auto PX = [&](int t, int c) -> double& {
+        return SLAB ? slab[t + (size_t)c * chunk] : P[(r0 + t) + (int64_t)c * ld];
+    };
+    if (SLAB) {
+        for (int c = warp; c < w; c += NW)
+            for (int t = lane; t < nr; t += 32) slab[t + (size_t)c * chunk] = P[(r0 + t) + (int64_t)c * ld];
+        __syncthreads();
+    }
 
     // ---- prologue: partials of column 0 ------------------------------------
     for (int t = tid; t < nr; t += PNT) {
         int r = r0 + t;
-        xsb0[t] = (r > 0) ? P[r] : 0.0;
+        xsb0[t] = (r > 0) ? PX(t, 0) : 0.0;
     }
     __syncthreads();
     for (int c = warp; c < w; c += NW) {
         double acc = 0.0;
         for (int t = lane; t < nr; t += 32) {
-            double y = (c == 0) ? xsb0[t] : P[(r0 + t) + (int64_t)c * ld];
+            double y = (c == 0) ? xsb0[t] : PX(t, c);
             acc += xsb0[t] * y;
         }
         acc = warp_sum(acc);
         if (lane == 0) part[(size_t)cta * w + c] = acc;
     }
     if (r0 <= 0 && 0 < r1)
-        for (int c = tid; c < w; c += PNT) piv[c] = P[(int64_t)c * ld];
+        for (int c = tid; c < w; c += PNT) piv[c] = PX(0, c);
     if (!grid_sync(bar, target, status)) return;
 
     for (int j = 0; j < w; ++j) {
@@ -113,10 +127,10 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
                 if (r > j) {
                     double v = xc[t] / d;
                     xc[t] = v;
-                    P[r + (int64_t)j * ld] = v;
+                    PX(t, j) = v;
                 }
             }
-            if (tid == 0 && r0 <= j && j < r1) P[j + (int64_t)j * ld] = beta;
+            if (tid == 0 && r0 <= j && j < r1) PX(j - r0, j) = beta;
         }
         __syncthreads();
         if (j + 1 >= w) break;
@@ -126,7 +140,7 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
             int r = r0 + t;
             double val = 0.0;
             if (r > j) {
-                double* e = P + r + (int64_t)(j + 1) * ld;
+                double* e = &PX(t, j + 1);
                 val = *e;
                 if (act) {
                     val -= tj * xc[t] * wv[j + 1];
@@ -136,7 +150,7 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
             xn[t] = (r > j + 1) ? val : 0.0;
         }
         if (act && r0 <= j && j < r1)
-            for (int c = j + 1 + tid; c < w; c += PNT) P[j + (int64_t)c * ld] = __ldcg(pv + c) - tj * wv[c];
+            for (int c = j + 1 + tid; c < w; c += PNT) PX(j - r0, c) = __ldcg(pv + c) - tj * wv[c];
         __syncthreads();
 
         // (b2) columns c >= j+2: apply H_j, accumulate the next column's partials
@@ -150,7 +164,7 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
                 for (int t = lane; t < nr; t += 32) {
                     int r = r0 + t;
                     if (r > j) {
-                        double* e = P + r + (int64_t)c * ld;
+                        double* e = &PX(t, c);
                         double val = *e;
                         if (act) {
                             val -= tj * xc[t] * wc;
@@ -166,8 +180,13 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
         __syncthreads();
         if (r0 <= j + 1 && j + 1 < r1)
             for (int c = j + 1 + tid; c < w; c += PNT)
-                piv[(size_t)(p ^ 1) * w + c] = P[(j + 1) + (int64_t)c * ld];
+                piv[(size_t)(p ^ 1) * w + c] = PX(j + 1 - r0, c);
         if (!grid_sync(bar, target, status)) return;
+    }
+    if (SLAB) {
+        __syncthreads();
+        for (int c = warp; c < w; c += NW)
+            for (int t = lane; t < nr; t += 32) P[(r0 + t) + (int64_t)c * ld] = slab[t + (size_t)c * chunk];
     }
 }
 
@@ -181,36 +200,40 @@ __global__ void k_extract_w(const double* __restrict__ P, int64_t ld, int len, i
     }
 }
 
-// Forward column-wise recurrence (Sec. 2.3 compact WY):
-//   Tf(j,j) = tau_j,  Tf(0:j, j) = -tau_j Tf(0:j, 0:j) (W^T W)(0:j, j).
-// One block; rows of the triangular mat-vec are spread over warps, the sum
-// over l over lanes.  Ts is a row-major working copy (shared memory when it
-// fits, else the caller's scratch passed as Tf's storage area).
-__global__ void __launch_bounds__(256) k_tfactor(const double* __restrict__ gram, const double* __restrict__ tau,
-                                                 int w, double* __restrict__ Tf, double* __restrict__ gscr,
-                                                 int use_smem, int* status) {
-    extern __shared__ double tsm[];
-    double* Ts = use_smem ? tsm : gscr;  // row-major: Ts[i*w + l]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < w * w; e += blockDim.x) Ts[e] = 0.0;
-    __syncthreads();
-    for (int j = 0; j < w; ++j) {
-        const double tj = tau[j];
-        for (int i = warp; i < j; i += 8) {
-            double s = 0.0;
-            for (int l = i + lane; l < j; l += 32) s += Ts[(size_t)i * w + l] * gram[l + (size_t)j * w];
-            s = warp_sum(s);
-            if (lane == 0) Ts[(size_t)i * w + j] = -tj * s;
-        }
-        if (tid == 0) {
-            Ts[(size_t)j * w + j] = tj;
-            if (!isfinite(tj)) atomicOr(status, ST_NONFINITE);
-        }
+// Triangular factor of the compact WY form (Sec. 2.3): Q = H_0 ... H_{w-1} =
+// I - W Tf W^T.  Tf is the inverse of S = diag(1 / tau) + strict_upper(W^T W)
+// (the column recurrence Tf(0:j, j) = -tau_j Tf(0:j,0:j) (W^T W)(0:j, j)
+// written as one triangular solve per column), so every column is an
+// independent back substitution:
+//   Tf(j, j) = tau_j,  Tf(i, j) = -tau_i sum_{k=i+1..j} (W^T W)(i, k) Tf(k, j),
+// which also holds for tau_i = 0 (H_i = I gives a zero row and column).
+// One thread per column; the Gram matrix is staged in shared memory when it
+// fits.
+__global__ void k_tfactor(const double* __restrict__ gram, const double* __restrict__ tau, int w,
+                          double* __restrict__ Tf, int use_smem, int* status) {
+    extern __shared__ double gsm[];
+    const double* G = gram;
+    if (use_smem) {
+        for (int e = threadIdx.x; e < w * w; e += blockDim.x) gsm[e] = gram[e];
         __syncthreads();
+        G = gsm;
     }
-    for (int e = tid; e < w * w; e += blockDim.x) {
-        int i = e % w, jj = e / w;
-        Tf[e] = Ts[(size_t)i * w + jj];
+    for (int j = threadIdx.x; j < w; j += blockDim.x) {
+        double* x = Tf + (size_t)j * w;
+        for (int i = j + 1; i < w; ++i) x[i] = 0.0;
+        const double tj = tau[j];
+        if (!isfinite(tj)) atomicOr(status, ST_NONFINITE);
+        x[j] = tj;
+        for (int i = j - 1; i >= 0; --i) {
+            double s0 = 0.0, s1 = 0.0;
+            int k = i + 1;
+            for (; k + 1 <= j; k += 2) {
+                s0 += G[i + (size_t)k * w] * x[k];
+                s1 += G[i + (size_t)(k + 1) * w] * x[k + 1];
+            }
+            if (k <= j) s0 += G[i + (size_t)k * w] * x[k];
+            x[i] = -tau[i] * (s0 + s1);
+        }
     }
 }
 
@@ -235,19 +258,23 @@ cudaError_t panel_qr(double* P, int64_t ld, int64_t len, int w, double* tau, dou
     if (chunk > kMaxChunk || G > sms) return cudaErrorInvalidValue;
     double* part = scratch;
     double* piv = scratch + (size_t)2 * G * w;
-    size_t shm = sizeof(double) * ((size_t)2 * chunk + (size_t)2 * w);
-    static thread_local size_t configured = 0;
-    if (shm > 48 * 1024 && shm > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_panel_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const size_t base = sizeof(double) * ((size_t)2 * chunk + (size_t)2 * w);
+    const size_t with_slab = base + sizeof(double) * (size_t)chunk * w;
+    const bool use_slab = with_slab <= 220 * 1024;
+    const size_t shm = use_slab ? with_slab : base;
+    const void* fn = use_slab ? (const void*)k_panel_qr<true> : (const void*)k_panel_qr<false>;
+    static thread_local size_t configured[2] = {0, 0};
+    if (shm > 48 * 1024 && shm > configured[use_slab]) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;
-        configured = shm;
+        configured[use_slab] = shm;
     }
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     int len_i = (int)len;
     void* args[] = {&P, &ld, &len_i, &w, &tau, &part, &piv, &bar, &status, &chunk};
     trace_count(1);
-    return cudaLaunchCooperativeKernel((const void*)k_panel_qr, dim3(G), dim3(PNT), args, shm, st);
+    return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(PNT), args, shm, st);
 }
 
 cudaError_t extract_w(const double* P, int64_t ld, int64_t len, int w, double* W, cudaStream_t st) {
@@ -261,19 +288,17 @@ cudaError_t extract_w(const double* P, int64_t ld, int64_t len, int w, double* W
 
 cudaError_t tfactor(const double* gram, const double* tau, int w, double* Tf, int* status, cudaStream_t st) {
     if (w <= 0) return cudaSuccess;
-    size_t bytes = sizeof(double) * (size_t)w * w;
-    int use_smem = bytes <= 200 * 1024;
-    // without shared memory the row-major working copy lives behind Tf's
-    // column-major result (the caller reserves 2 w^2 doubles).
-    double* gscr = Tf + (size_t)w * w;
-    size_t shm = use_smem ? bytes : 0;
+    const size_t bytes = sizeof(double) * (size_t)w * w;
+    const int use_smem = bytes <= 200 * 1024;
+    const size_t shm = use_smem ? bytes : 0;
     static thread_local size_t configured = 0;
     if (shm > 48 * 1024 && shm > configured) {
         cudaError_t e = cudaFuncSetAttribute(k_tfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;
         configured = shm;
     }
-    k_tfactor<<<1, 256, shm, st>>>(gram, tau, w, Tf, gscr, use_smem, status);
+    const int threads = std::min(1024, ((w + 31) / 32) * 32);
+    k_tfactor<<<1, threads, shm, st>>>(gram, tau, w, Tf, use_smem, status);
     trace_count(1);
     return cudaGetLastError();
 }

@@ -53,6 +53,7 @@ struct Workspace {
     double* dq;       // candidate diagonals, 4 x w (trace mode)
     float* qmodel;    // network parameters on the device
     void* oz;         // digit slices and exponents of the emulated FP64 products
+    size_t oz_bytes;
 };
 
 constexpr int kSlots = 29;
@@ -165,6 +166,7 @@ Workspace carve(void* base, const Layout& L) {
     w.dq = (double*)(p + L.off[26] + sizeof(float) * 32);
     w.qmodel = (float*)(p + L.off[27]);
     w.oz = (void*)(p + L.off[28]);
+    w.oz_bytes = L.total - L.off[28];
     return w;
 }
 
@@ -228,7 +230,8 @@ cudaError_t gemm(Ctx& c, const char* role, bool ta, bool tb, int64_t M, int64_t 
     double bytes = 8.0 * ((double)M * K + (double)K * N + (double)M * N * (beta != 0.0 ? 2.0 : 1.0));
     TraceScope ts(role, flops, bytes, c.st);
     if (emulated_prec(c.prec) && M >= 128 && N >= 64 && K >= 64)
-        return oz_gemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.w.oz, c.w.status, c.st);
+        return oz_gemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.w.oz, c.w.oz_bytes, c.sms, c.w.status,
+                       c.st);
     return gemm_f64(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.w.part, c.w.part_elems, c.sms, c.st);
 }
 

@@ -15,14 +15,24 @@
 //
 // GB300 design: FP64 runs at ~7 GFLOP/s per SM, so a single block would need
 // tens of milliseconds for b = 128.  The w/2 disjoint pairs of every round of
-// a round-robin ("circle") ordering are instead spread over w/2 blocks of one
-// cooperative launch, one pair per block, one row per thread, with A and V
-// resident in L2; one grid barrier separates rounds.  The pair order differs
-// from a cyclic-by-rows sweep, which changes only rounding: the converged,
-// canonical SVD is the same.
+// a round-robin ("circle") ordering are spread over many SMs instead:
+//   - k_jacobi_cluster (default): one 8-block thread-block cluster; A and V
+//     live in the blocks' shared memory, each warp rotates one pair per round
+//     through distributed shared memory, the hardware cluster barrier
+//     separates rounds;
+//   - k_jacobi: w/2 blocks of one cooperative launch, one pair per block, A
+//     and V in an L2-resident global scratch, a software grid barrier between
+//     rounds (used when the cluster's shared memory is too small, and by the
+//     allocation-free entry point).
+// The pair order differs from a cyclic-by-rows sweep, which changes only
+// rounding: the converged, canonical SVD is the same.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.h"
 #include "trace.h"
+
+namespace cg = cooperative_groups;
 
 namespace rutv {
 
@@ -188,18 +198,194 @@ __global__ void __launch_bounds__(NT) k_jacobi(const double* __restrict__ R, int
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Cluster variant: one thread-block cluster of JC_CTAS blocks.  Column c of
+// the working copies A and V lives in the shared memory of block
+// c / cols_per_block; every round each warp rotates one pair (p, q) of the
+// circle ordering through distributed shared memory (its lanes own rows), and
+// the hardware cluster barrier separates rounds.  Same schedule, rotation and
+// canonical output as k_jacobi; only the order of the three dot-product sums
+// differs (rounding).
+constexpr int JC_CTAS = 8;
+constexpr int JC_THREADS = 256;
+
+__global__ void __cluster_dims__(JC_CTAS, 1, 1) __launch_bounds__(JC_THREADS)
+    k_jacobi_cluster(const double* __restrict__ R, int64_t ldr, int w, int n2, int cpb, double* __restrict__ D,
+                     double* __restrict__ Us, double* __restrict__ Vs, int* status, int max_sweeps, double tol) {
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ double jsm[];
+    double* Aloc = jsm;                       // cpb columns x w
+    double* Vloc = jsm + (size_t)cpb * w;     // cpb columns x w
+    double* nrm = Vloc + (size_t)cpb * w;     // cpb norms
+    __shared__ int s_flag;
+    const int me = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int NWALL = JC_CTAS * (JC_THREADS / 32);
+
+    for (int lc = 0; lc < cpb; ++lc) {
+        const int c = me * cpb + lc;
+        for (int r = tid; r < w; r += JC_THREADS) {
+            Aloc[(size_t)lc * w + r] = (c < w && r <= c) ? R[r + (int64_t)c * ldr] : 0.0;
+            Vloc[(size_t)lc * w + r] = (r == c) ? 1.0 : 0.0;
+        }
+    }
+    auto colA = [&](int c) -> double* {
+        return cluster.map_shared_rank(Aloc, c / cpb) + (size_t)(c % cpb) * w;
+    };
+    auto colV = [&](int c) -> double* {
+        return cluster.map_shared_rank(Vloc, c / cpb) + (size_t)(c % cpb) * w;
+    };
+    cluster.sync();
+
+    bool converged = (w <= 1);
+    for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+        if (tid == 0) s_flag = 0;
+        cluster.sync();
+        for (int round = 0; round < n2 - 1; ++round) {
+            for (int k = me * (JC_THREADS / 32) + warp; k < n2 / 2; k += NWALL) {
+                int p = circle_elem(k, round, n2);
+                int q = circle_elem(n2 - 1 - k, round, n2);
+                if (p > q) { int t = p; p = q; q = t; }
+                if (q >= w) continue;
+                double* ap = colA(p);
+                double* aq = colA(q);
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int r = lane; r < w; r += 32) {
+                    double x = ap[r], y = aq[r];
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                ga = warp_sum(ga);
+                if (!isfinite(al) || !isfinite(be) || !isfinite(ga)) {
+                    if (lane == 0) atomicOr(status, ST_NONFINITE);
+                    continue;
+                }
+                if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) continue;
+                double zeta = (be - al) / (2.0 * ga);
+                double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double cs = 1.0 / sqrt(1.0 + t * t);
+                double sn = cs * t;
+                double* vp = colV(p);
+                double* vq = colV(q);
+                for (int r = lane; r < w; r += 32) {
+                    double x = ap[r], y = aq[r];
+                    ap[r] = cs * x - sn * y;
+                    aq[r] = sn * x + cs * y;
+                    double u = vp[r], z = vq[r];
+                    vp[r] = cs * u - sn * z;
+                    vq[r] = sn * u + cs * z;
+                }
+                if (lane == 0) s_flag = 1;
+            }
+            cluster.sync();
+        }
+        int any = 0;
+        for (int b = 0; b < JC_CTAS; ++b) any |= *cluster.map_shared_rank(&s_flag, b);
+        converged = (any == 0);
+        cluster.sync();  // every block has read the flags before they are reset
+    }
+    if (!converged && me == 0 && tid == 0) atomicOr(status, ST_NOCONV);
+
+    // ---- canonical output: each block writes its own columns ---------------
+    for (int lc = warp; lc < cpb; lc += JC_THREADS / 32) {
+        double s2 = 0.0;
+        for (int r = lane; r < w; r += 32) s2 += Aloc[(size_t)lc * w + r] * Aloc[(size_t)lc * w + r];
+        s2 = warp_sum(s2);
+        if (lane == 0) nrm[lc] = sqrt(s2);
+    }
+    cluster.sync();
+    for (int lc = warp; lc < cpb; lc += JC_THREADS / 32) {
+        const int c = me * cpb + lc;
+        if (c >= w) continue;
+        const double v = nrm[lc];
+        int rank = 0;
+        for (int c2 = lane; c2 < w; c2 += 32) {
+            const double u = *(cluster.map_shared_rank(nrm, c2 / cpb) + (c2 % cpb));
+            rank += (u > v) || (u == v && c2 < c);
+        }
+        for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+        // canonical sign: largest |Vs| entry (lowest index on ties) positive
+        double vmax = -1.0;
+        int imax = 0;
+        for (int r = lane; r < w; r += 32) {
+            double a = fabs(Vloc[(size_t)lc * w + r]);
+            if (a > vmax) { vmax = a; imax = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(0xffffffffu, vmax, o);
+            int oi = __shfl_xor_sync(0xffffffffu, imax, o);
+            if (ov > vmax || (ov == vmax && oi < imax)) { vmax = ov; imax = oi; }
+        }
+        const double sg = (Vloc[(size_t)lc * w + imax] < 0.0) ? -1.0 : 1.0;
+        if (lane == 0) D[rank] = v;
+        for (int r = lane; r < w; r += 32) {
+            Vs[r + (size_t)rank * w] = sg * Vloc[(size_t)lc * w + r];
+            Us[r + (size_t)rank * w] = (v > 0.0) ? sg * Aloc[(size_t)lc * w + r] / v : 0.0;
+        }
+    }
+    __threadfence();
+    cluster.sync();
+    // left vectors of zero singular values: Gram-Schmidt (twice) on unit
+    // vectors, then the pair's canonical sign (block 0, rare)
+    if (me == 0 && tid == 0) {
+        for (int j = 0; j < w; ++j) {
+            if (D[j] > 0.0) continue;
+            double* u = Us + (size_t)j * w;
+            for (int e = 0; e < w; ++e) {
+                for (int r = 0; r < w; ++r) u[r] = (r == e) ? 1.0 : 0.0;
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int l = 0; l < w; ++l) {
+                        if (l == j || (D[l] == 0.0 && l > j)) continue;
+                        const double* ul = Us + (size_t)l * w;
+                        double d = 0.0;
+                        for (int r = 0; r < w; ++r) d += ul[r] * u[r];
+                        for (int r = 0; r < w; ++r) u[r] -= d * ul[r];
+                    }
+                double nn = 0.0;
+                for (int r = 0; r < w; ++r) nn += u[r] * u[r];
+                nn = sqrt(nn);
+                if (nn > 0.5) {
+                    for (int r = 0; r < w; ++r) u[r] /= nn;
+                    break;
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
 
 size_t jacobi_scratch_elems(int w) { return (size_t)2 * w * w; }
 
 cudaError_t jacobi_svd(const double* R, int64_t ldr, int w, double* D, double* Us, double* Vs, double* scratch,
-                       unsigned* bar, int* counters, int* status, int max_sweeps, cudaStream_t st) {
+                       unsigned* bar, int* counters, int* status, int max_sweeps, cudaStream_t st,
+                       bool allow_cluster) {
     if (w <= 0) return cudaSuccess;
     int n2 = w + (w & 1);
+    double tol = (double)w * 1.1102230246251565e-16;
+    // cluster variant when A and V fit in the cluster's shared memory
+    const int cpb = (n2 + JC_CTAS - 1) / JC_CTAS;
+    const size_t shm_cluster = sizeof(double) * ((size_t)2 * cpb * w + cpb);
+    if (allow_cluster && shm_cluster <= 200 * 1024) {
+        static thread_local size_t configured = 0;
+        if (shm_cluster > 48 * 1024 && shm_cluster > configured) {
+            cudaError_t e =
+                cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_cluster);
+            if (e != cudaSuccess) return e;
+            configured = shm_cluster;
+        }
+        trace_count(1);
+        k_jacobi_cluster<<<JC_CTAS, JC_THREADS, shm_cluster, st>>>(R, ldr, w, n2, cpb, D, Us, Vs, status, max_sweeps,
+                                                                    tol);
+        return cudaGetLastError();
+    }
     int G = std::max(1, n2 / 2);
     double* A = scratch;
     double* V = scratch + (size_t)w * w;
-    double tol = (double)w * 1.1102230246251565e-16;
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     size_t shm = sizeof(double) * (size_t)w;

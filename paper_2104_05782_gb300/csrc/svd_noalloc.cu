@@ -55,7 +55,8 @@ extern "C" randutv_status randutv_svd_small_noalloc(int w, const double* R, int6
     // the barrier counter is zeroed by the launcher, the rotation counters by
     // the kernel itself; the status word is cleared here
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return RANDUTV_ECUDA;
-    if (jacobi_svd(R, ldr, w, D, Us, Vs, base, bar, counters, status, 30, st) != cudaSuccess) return RANDUTV_ECUDA;
+    if (jacobi_svd(R, ldr, w, D, Us, Vs, base, bar, counters, status, 30, st, /*allow_cluster=*/false) != cudaSuccess)
+        return RANDUTV_ECUDA;
     int bits = 0;
     if (cudaMemcpyAsync(&bits, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return RANDUTV_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return RANDUTV_ECUDA;
