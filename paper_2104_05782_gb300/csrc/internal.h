@@ -84,6 +84,25 @@ cudaError_t learnq_predict(const float* P, const float* X, int N, float* probs, 
 // ---- FP64 products emulated on BF16 tensor cores (oz_gemm.cu) ---------------
 int64_t oz_ldq(int64_t K);
 size_t oz_work_bytes(int64_t M, int64_t N, int64_t K);
+// One operand split into OZ_S = 8 BF16 digit planes with a power-of-two
+// scale per row: L(r, k) = trans ? X(k, r) : X(r, k), r < R, k < K.  Plane s
+// holds rows [s * plane, s * plane + R) of a row-major array with ldq BF16
+// per row; e[r] is the row's scale exponent.
+struct OzOperand {
+    const uint16_t* Q;
+    const int* e;
+    int64_t R, K, plane, ldq;
+};
+size_t oz_operand_bytes(int64_t R, int64_t K);
+// Splits X into `buf` (oz_operand_bytes(R, K) bytes, 256-byte aligned).
+cudaError_t oz_split(bool trans, const double* X, int64_t ldx, int64_t R, int64_t K, void* buf, OzOperand* out,
+                     int* status, cudaStream_t st);
+// C (M x N) = alpha La(a_row0 : a_row0 + M, :) Lb(b_row0 : b_row0 + N, :)^T + beta C
+// from split operands; needs M >= 128, N >= 64, K >= 64; P holds the FP64
+// split-K partials (p_bytes bytes; too few bytes means no split-K).
+cudaError_t oz_product(const OzOperand& a, int64_t a_row0, const OzOperand& b, int64_t b_row0, int64_t M, int64_t N,
+                       double alpha, double beta, double* C, int64_t ldc, double* P, size_t p_bytes, int sms,
+                       int* status, cudaStream_t st);
 // Needs M >= 128, N >= 64, K >= 64; `work` holds oz_work_bytes(M, N, K) bytes
 // (digits, exponents and the FP64 split-K partials).
 cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,

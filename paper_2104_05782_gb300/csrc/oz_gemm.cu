@@ -12,7 +12,8 @@
 // With S = 8 digits (56 bits) and the digit pairs s + t <= S + 1 kept, the
 // error is about K 2^{-56} max|op(A)(r,:)| max|op(B)(:,c)| (digit truncation;
 // the dropped pairs weigh 2^{-70}).  One tcgen05 accumulator per digit sum d
-// lives in TMEM (8 x 64 FP32 columns = all 512); every 128 of K the partial
+// lives in TMEM (8 x TN FP32 columns: all 512 for TN = 64, 256 for the
+// TN = 32 tiles of short-K products, two CTAs per SM); every 128 of K the partial
 // sums are exact integers in FP32 (<= 8 pairs x 128 x 127^2 < 2^24), and they
 // are folded into double-float (hi, lo) FP32 registers with exact
 // power-of-two weights.  The final value gets one FP64 epilogue per element.
@@ -21,6 +22,9 @@
 // (GB300's FP64 pipe would make a floating-point split cost more than the
 // product): significand m (53 bits), exponent E; the row scale eA_r is the
 // largest E+1 of the row; the digits are the top 7S bits of m aligned to it.
+// A split operand (OzOperand) can serve several products: its digit planes
+// are addressed by a row offset, so a split of T(:, k0:n) by rows also
+// serves products with the row block T(k0:m, k0:n).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -35,7 +39,7 @@ namespace {
 
 constexpr int OZ_S = 8;         // digits per operand
 constexpr int OZ_TM = 128;      // output rows per CTA (UMMA M)
-constexpr int OZ_TN = 64;       // output columns per CTA (UMMA N)
+constexpr int OZ_TN = 64;       // output columns per CTA (UMMA N); 32 for short-K products
 constexpr int OZ_TK = 64;       // K per stage (128 bytes of BF16)
 constexpr int OZ_CHUNK = 2;     // k-blocks per exact FP32 chunk (K = 128)
 constexpr int OZ_THREADS = 192; // warps 0-3 drain TMEM, warp 4 = TMA, warp 5 = MMA
@@ -185,24 +189,43 @@ __global__ void k_oz_split(const double* __restrict__ X, int64_t ld, int R, int 
 }
 
 // ---------------------------------------------------------------- product
+template <int TN>
 struct OzSmem {
     static constexpr int A_BYTES = OZ_TM * OZ_TK * 2;           // 16 KB
-    static constexpr int B_BYTES = OZ_TN * OZ_TK * 2;           // 8 KB
-    static constexpr int B_SET = OZ_S * B_BYTES;                // 56 KB
+    static constexpr int B_BYTES = TN * OZ_TK * 2;              // 8 KB (TN = 64)
+    static constexpr int B_SET = OZ_S * B_BYTES;                // 64 KB (TN = 64)
     static constexpr int TOTAL = 2 * A_BYTES + 2 * B_SET + 1024 + 256;
+    static constexpr uint32_t TMEM_COLS = OZ_S * TN;            // 512 or 256
 };
 
-__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant__ CUtensorMap mapA,
+// FP32 value x times 2^sh, built as an FP64 bit pattern with integer
+// instructions (exact); zero and FP32 subnormals give 0; returns false when
+// the result would leave the FP64 normal range.
+__device__ __forceinline__ bool f32_to_f64_scaled(float x, int sh, double& out) {
+    const uint32_t u = __float_as_uint(x);
+    const int e8 = (int)((u >> 23) & 0xFF);
+    if (e8 == 0) { out = 0.0; return true; }
+    const int e = e8 - 127 + 1023 + sh;
+    if (e <= 0 || e >= 2047) return false;
+    out = __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | ((unsigned long long)e << 52) |
+                                           ((unsigned long long)(u & 0x7FFFFF) << 29)));
+    return true;
+}
+
+template <int TN, int MINB>
+__global__ void __launch_bounds__(OZ_THREADS, MINB) k_oz_gemm(const __grid_constant__ CUtensorMap mapA,
                                                            const __grid_constant__ CUtensorMap mapB, int M, int N,
                                                            int K, const int* __restrict__ eA,
                                                            const int* __restrict__ eB, double alpha, double beta,
                                                            double* __restrict__ C, int64_t ldc, int kbs,
-                                                           double* __restrict__ P, int* status) {
+                                                           double* __restrict__ P, int* status, int a_plane,
+                                                           int a_row0, int b_plane, int b_row0) {
+    using L = OzSmem<TN>;
     extern __shared__ __align__(1024) uint8_t oz_raw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)oz_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* Abuf = sm;                                   // 2 x A_BYTES
-    uint8_t* Bbuf = sm + 2 * OzSmem::A_BYTES;             // 2 x B_SET
-    uint64_t* bars = (uint64_t*)(sm + 2 * OzSmem::A_BYTES + 2 * OzSmem::B_SET);
+    uint8_t* Abuf = sm;                               // 2 x A_BYTES
+    uint8_t* Bbuf = sm + 2 * L::A_BYTES;              // 2 x B_SET
+    uint64_t* bars = (uint64_t*)(sm + 2 * L::A_BYTES + 2 * L::B_SET);
     uint64_t* a_full = bars;       // [2]
     uint64_t* a_empty = bars + 2;  // [2]
     uint64_t* b_full = bars + 4;   // [2]
@@ -213,7 +236,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
     __shared__ volatile int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * OZ_TM, n0 = blockIdx.y * OZ_TN;
+    const int m0 = blockIdx.x * OZ_TM, n0 = blockIdx.y * TN;
     // split z covers k-blocks [kb0, kb0 + nkb); gridDim.z > 1 writes FP64 partials to P
     const int nkb_all = (K + OZ_TK - 1) / OZ_TK;
     const int kb0 = blockIdx.z * kbs;
@@ -235,7 +258,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
-                     "r"(512u)
+                     "r"(L::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -251,15 +274,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                 kb_done = kb + 1;
                 const int sb = kb & 1;
                 if (!bar_wait(&b_empty[sb], (uint32_t)(((kb >> 1) & 1) ^ 1))) { s_abort = 1; break; }
-                bar_expect(&b_full[sb], (uint32_t)OzSmem::B_SET);
+                bar_expect(&b_full[sb], (uint32_t)L::B_SET);
                 for (int t = 0; t < OZ_S; ++t)
-                    tma2d(Bbuf + sb * OzSmem::B_SET + t * OzSmem::B_BYTES, &mapB, &b_full[sb], (kb0 + kb) * OZ_TK,
-                          t * N + n0);
+                    tma2d(Bbuf + sb * L::B_SET + t * L::B_BYTES, &mapB, &b_full[sb], (kb0 + kb) * OZ_TK,
+                          t * b_plane + b_row0 + n0);
                 for (int s = 0; s < OZ_S; ++s, ++ia) {
                     const int sa = ia & 1;
                     if (!bar_wait(&a_empty[sa], (uint32_t)(((ia >> 1) & 1) ^ 1))) { s_abort = 1; break; }
-                    bar_expect(&a_full[sa], (uint32_t)OzSmem::A_BYTES);
-                    tma2d(Abuf + sa * OzSmem::A_BYTES, &mapA, &a_full[sa], (kb0 + kb) * OZ_TK, s * M + m0);
+                    bar_expect(&a_full[sa], (uint32_t)L::A_BYTES);
+                    tma2d(Abuf + sa * L::A_BYTES, &mapA, &a_full[sa], (kb0 + kb) * OZ_TK, s * a_plane + a_row0 + m0);
                 }
             }
             // every copy issued must land before the CTA can exit
@@ -268,7 +291,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
         }
     } else if (warp == 5) {
         if (lane == 0 && nkb > 0) {  // ---------------- MMA issuer
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_TN >> 3) << 17) |
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                                    ((uint32_t)(OZ_TM >> 4) << 24);
             int ia = 0, chunk = 0;
             for (int kb = 0; kb < nkb && !s_abort; ++kb) {
@@ -283,10 +306,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                     const int sa = ia & 1;
                     if (!bar_wait(&a_full[sa], (uint32_t)((ia >> 1) & 1))) { s_abort = 1; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint64_t da = desc_sw128(su32(Abuf + sa * OzSmem::A_BYTES));
+                    const uint64_t da = desc_sw128(su32(Abuf + sa * L::A_BYTES));
                     for (int t = 0; t + s < OZ_S; ++t) {
-                        const uint64_t db = desc_sw128(su32(Bbuf + sb * OzSmem::B_SET + t * OzSmem::B_BYTES));
-                        const uint32_t dt = tmem + (uint32_t)((s + t) * OZ_TN);
+                        const uint64_t db = desc_sw128(su32(Bbuf + sb * L::B_SET + t * L::B_BYTES));
+                        const uint32_t dt = tmem + (uint32_t)((s + t) * TN);
 #pragma unroll
                         for (int k = 0; k < OZ_TK / 16; ++k) {
                             const uint64_t ko = (uint64_t)((k * 32) >> 4);
@@ -314,9 +337,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
             }
         }
     } else {  // ---------------- warps 0-3: drain TMEM into double-float
-        float hi[OZ_TN], lo[OZ_TN];
+        float hi[TN], lo[TN];
 #pragma unroll
-        for (int j = 0; j < OZ_TN; ++j) hi[j] = lo[j] = 0.0f;
+        for (int j = 0; j < TN; ++j) hi[j] = lo[j] = 0.0f;
         bool ok = true;
         for (int ch = 0; ch < nchunks; ++ch) {
             ok = __all_sync(0xffffffffu, bar_wait(c_full, (uint32_t)(ch & 1)));
@@ -326,9 +349,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
             for (int d = OZ_S - 1; d >= 0; --d) {
                 const float w = __int_as_float((127 - 7 * (d + 2)) << 23);  // 2^{-7(d+2)}
 #pragma unroll
-                for (int c0 = 0; c0 < OZ_TN; c0 += 32) {
+                for (int c0 = 0; c0 < TN; c0 += 32) {
                     uint32_t v[32];
-                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * OZ_TN + c0);
+                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TN + c0);
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
                         "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -349,7 +372,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                 }
             }
 #pragma unroll
-            for (int j = 0; j < OZ_TN; ++j) {  // renormalise (fast two-sum)
+            for (int j = 0; j < TN; ++j) {  // renormalise (fast two-sum)
                 float s = hi[j] + lo[j];
                 lo[j] = lo[j] - (s - hi[j]);
                 hi[j] = s;
@@ -362,20 +385,31 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
         double* Pz = partial ? P + (size_t)blockIdx.z * (size_t)M * (size_t)N : nullptr;
         if (ok && !s_abort && r < M) {
             const int er = eA[r];
+            // alpha = +-1 folds into the sign; beta in {0, 1} needs no multiply
+            const bool unit_alpha = (alpha == 1.0 || alpha == -1.0);
+            const unsigned long long sgn = (alpha < 0.0) ? (1ull << 63) : 0ull;
 #pragma unroll
-            for (int j = 0; j < OZ_TN; ++j) {
+            for (int j = 0; j < TN; ++j) {
                 const int c = n0 + j;
                 if (c >= N) break;
-                double* cp = C + r + (int64_t)c * ldc;
                 const int ec = eB[c];
                 double v = 0.0;
                 if (er != INT_MIN && ec != INT_MIN) {
-                    // 2^{er+ec} built from its bits (|er + ec| stays far inside the normal range)
-                    const double scale = __longlong_as_double((long long)(er + ec + 1023) << 52) * alpha;
-                    v = fma((double)hi[j], scale, (double)lo[j] * scale);
+                    double dh, dl;
+                    if (unit_alpha && f32_to_f64_scaled(hi[j], er + ec, dh) && f32_to_f64_scaled(lo[j], er + ec, dl)) {
+                        v = __longlong_as_double(__double_as_longlong(dh) ^ (long long)sgn) +
+                            __longlong_as_double(__double_as_longlong(dl) ^ (long long)sgn);
+                    } else {  // general alpha or extreme exponents
+                        const double scale = ldexp(alpha, er + ec);
+                        v = fma((double)hi[j], scale, (double)lo[j] * scale);
+                    }
                 }
-                if (partial) Pz[r + (size_t)c * M] = v;
-                else *cp = (beta == 0.0) ? v : fma(beta, *cp, v);
+                if (partial) {
+                    Pz[r + (size_t)c * M] = v;
+                } else {
+                    double* cp = C + r + (int64_t)c * ldc;
+                    *cp = (beta == 0.0) ? v : (beta == 1.0 ? *cp + v : fma(beta, *cp, v));
+                }
             }
         }
     }
@@ -383,7 +417,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TMEM_COLS) : "memory");
 }
 
 // C = sum_z P[z] (fixed order) + beta C
@@ -429,10 +463,17 @@ unsigned oz_grid(int64_t total) { return (unsigned)std::max<int64_t>(1, std::min
 
 int64_t oz_ldq(int64_t K) { return (K + 63) / 64 * 64; }
 
+// short-K products with many output tiles (the rank-b updates) use 32-column
+// tiles: 256 TMEM columns and ~97 KB of shared memory let two CTAs share an
+// SM, so one's epilogue overlaps the other's MMAs
+int oz_tn(int64_t M, int64_t N, int64_t K, int sms) {
+    return (K <= 256 && cdiv(M, OZ_TM) * cdiv(N, 64) >= 4LL * sms) ? 32 : 64;
+}
+
 // split-K factor: slices of whole 128-deep chunks until the grid covers the
 // SMs about twice; partials (FP64) need splits * M * N doubles
 int oz_splits(int64_t M, int64_t N, int64_t K, int sms) {
-    const int64_t tiles = cdiv(M, OZ_TM) * cdiv(N, OZ_TN);
+    const int64_t tiles = cdiv(M, OZ_TM) * cdiv(N, oz_tn(M, N, K, sms));
     const int64_t chunks = cdiv(cdiv(K, OZ_TK), OZ_CHUNK);
     int64_t s = 1;
     if (tiles < 2LL * sms) s = cdiv(2LL * sms, tiles);
@@ -442,10 +483,79 @@ int oz_splits(int64_t M, int64_t N, int64_t K, int sms) {
     return (int)std::max<int64_t>(s, 1);
 }
 
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t oz_operand_bytes(int64_t R, int64_t K) {
+    return align256(sizeof(uint16_t) * (size_t)OZ_S * (size_t)R * (size_t)oz_ldq(K)) + align256(sizeof(int) * (size_t)R);
+}
+
 size_t oz_work_bytes(int64_t M, int64_t N, int64_t K) {
+    return oz_operand_bytes(M, K) + oz_operand_bytes(N, K) + 256 + sizeof(double) * ((size_t)1 << 27);
+}
+
+cudaError_t oz_split(bool trans, const double* X, int64_t ldx, int64_t R, int64_t K, void* buf, OzOperand* out,
+                     int* status, cudaStream_t st) {
     const int64_t ldq = oz_ldq(K);
-    return (size_t)OZ_S * 2 * ((size_t)M * ldq + (size_t)N * ldq) + 4 * (size_t)(M + N) + 1024 +
-           sizeof(double) * ((size_t)1 << 27);
+    uint16_t* Q = (uint16_t*)buf;
+    int* e = (int*)((char*)buf + align256(sizeof(uint16_t) * (size_t)OZ_S * (size_t)R * (size_t)ldq));
+    *out = OzOperand{Q, e, R, K, R, ldq};
+    if (R <= 0 || K <= 0) return cudaSuccess;
+    if (trans) {
+        k_oz_rowexp<<<(unsigned)std::min<int64_t>(cdiv(R, 8), 4096), 256, 0, st>>>(X, ldx, (int)R, (int)K, true, e,
+                                                                                      status);
+        k_oz_split<<<oz_grid(R * K), 256, 0, st>>>(X, ldx, (int)R, (int)K, true, e, Q, ldq);
+    } else {
+        k_oz_rowexp<<<(unsigned)cdiv(R, 32), 256, 0, st>>>(X, ldx, (int)R, (int)K, false, e, status);
+        k_oz_split<<<dim3((unsigned)cdiv(R, 32), (unsigned)cdiv(K, 32)), 256, 0, st>>>(X, ldx, (int)R, (int)K, false,
+                                                                                        e, Q, ldq);
+    }
+    trace_count(2);
+    return cudaGetLastError();
+}
+
+cudaError_t oz_product(const OzOperand& a, int64_t a_row0, const OzOperand& b, int64_t b_row0, int64_t M, int64_t N,
+                       double alpha, double beta, double* C, int64_t ldc, double* P, size_t p_bytes, int sms,
+                       int* status, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const int64_t K = a.K;
+    if (b.K != K || a_row0 < 0 || b_row0 < 0 || a_row0 + M > a.R || b_row0 + N > b.R) return cudaErrorInvalidValue;
+    if (M < OZ_TM || N < OZ_TN || K < OZ_TK) return cudaErrorInvalidValue;  // one TMA box at least
+    const int tn = oz_tn(M, N, K, sms);
+    int splits = oz_splits(M, N, K, sms);
+    if (sizeof(double) * (size_t)splits * M * N > p_bytes) splits = 1;
+    CUtensorMap ma, mb;
+    if (!oz_map(&ma, a.Q, (int64_t)OZ_S * a.plane, K, a.ldq, OZ_TM)) return cudaErrorInvalidValue;
+    if (!oz_map(&mb, b.Q, (int64_t)OZ_S * b.plane, K, b.ldq, tn)) return cudaErrorInvalidValue;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             OzSmem<64>::TOTAL);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_oz_gemm<32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     OzSmem<32>::TOTAL);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int64_t nkb = cdiv(K, OZ_TK);
+    const int kbs = (int)(cdiv(cdiv(nkb, OZ_CHUNK), splits) * OZ_CHUNK);  // whole chunks per split
+    splits = (int)cdiv(nkb, kbs);
+    dim3 grid((unsigned)cdiv(M, OZ_TM), (unsigned)cdiv(N, tn), (unsigned)splits);
+    const int* eA = a.e + a_row0;
+    const int* eB = b.e + b_row0;
+    if (tn == 32)
+        k_oz_gemm<32, 2><<<grid, OZ_THREADS, OzSmem<32>::TOTAL, st>>>(
+            ma, mb, (int)M, (int)N, (int)K, eA, eB, alpha, beta, C, ldc, kbs, P, status, (int)a.plane, (int)a_row0,
+            (int)b.plane, (int)b_row0);
+    else
+        k_oz_gemm<64, 1><<<grid, OZ_THREADS, OzSmem<64>::TOTAL, st>>>(
+            ma, mb, (int)M, (int)N, (int)K, eA, eB, alpha, beta, C, ldc, kbs, P, status, (int)a.plane, (int)a_row0,
+            (int)b.plane, (int)b_row0);
+    trace_count(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || splits == 1) return e;
+    k_oz_reduce<<<oz_grid(M * N), 256, 0, st>>>((int)M, (int)N, splits, P, beta, C, ldc);
+    trace_count(1);
+    return cudaGetLastError();
 }
 
 cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
@@ -453,63 +563,19 @@ cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double al
                     int sms, int* status, cudaStream_t st) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (M < OZ_TM || N < OZ_TN || K < OZ_TK) return cudaErrorInvalidValue;  // one TMA box at least
-    const int64_t ldq = oz_ldq(K);
-    uint16_t* QA = (uint16_t*)work;
-    uint16_t* QB = QA + (size_t)OZ_S * M * ldq;
-    int* eA = (int*)(QB + (size_t)OZ_S * N * ldq);
-    int* eB = eA + M;
-    double* P = (double*)(((uintptr_t)(eB + N) + 255) & ~(uintptr_t)255);
-    int splits = oz_splits(M, N, K, sms);
-    const size_t used = (size_t)((char*)P - (char*)work);
-    if (used + sizeof(double) * (size_t)splits * M * N > work_bytes) splits = 1;
-    // op(A) (M x K): row r = trans ? column r of A : row r of A
-    // op(B) (K x N) viewed as N x K K-major: row c = tb ? row c of B... : column c of B
-    const bool a_rows_contig = ta;   // op(A)(r,k) = A(k,r)
-    const bool b_rows_contig = !tb;  // Bk(c,k) = op(B)(k,c) = B(k,c)  (tb: B(c,k))
-    if (a_rows_contig)
-        k_oz_rowexp<<<(unsigned)std::min<int64_t>(cdiv(M, 8), 4096), 256, 0, st>>>(A, lda, (int)M, (int)K, true, eA,
-                                                                                      status);
-    else
-        k_oz_rowexp<<<(unsigned)cdiv(M, 32), 256, 0, st>>>(A, lda, (int)M, (int)K, false, eA, status);
-    if (b_rows_contig)
-        k_oz_rowexp<<<(unsigned)std::min<int64_t>(cdiv(N, 8), 4096), 256, 0, st>>>(B, ldb, (int)N, (int)K, true, eB,
-                                                                                      status);
-    else
-        k_oz_rowexp<<<(unsigned)cdiv(N, 32), 256, 0, st>>>(B, ldb, (int)N, (int)K, false, eB, status);
-    if (a_rows_contig)
-        k_oz_split<<<oz_grid(M * K), 256, 0, st>>>(A, lda, (int)M, (int)K, true, eA, QA, ldq);
-    else
-        k_oz_split<<<dim3((unsigned)cdiv(M, 32), (unsigned)cdiv(K, 32)), 256, 0, st>>>(A, lda, (int)M, (int)K, false,
-                                                                                        eA, QA, ldq);
-    if (b_rows_contig)
-        k_oz_split<<<oz_grid(N * K), 256, 0, st>>>(B, ldb, (int)N, (int)K, true, eB, QB, ldq);
-    else
-        k_oz_split<<<dim3((unsigned)cdiv(N, 32), (unsigned)cdiv(K, 32)), 256, 0, st>>>(B, ldb, (int)N, (int)K, false,
-                                                                                        eB, QB, ldq);
-    trace_count(4);
-    cudaError_t e = cudaGetLastError();
+    // op(A) row r = column r of A when ta; op(B) column c = column c of B unless tb
+    char* p = (char*)work;
+    OzOperand a, b;
+    cudaError_t e = oz_split(ta, A, lda, M, K, p, &a, status, st);
     if (e != cudaSuccess) return e;
-    CUtensorMap ma, mb;
-    if (!oz_map(&ma, QA, (int64_t)OZ_S * M, K, ldq, OZ_TM)) return cudaErrorInvalidValue;
-    if (!oz_map(&mb, QB, (int64_t)OZ_S * N, K, ldq, OZ_TN)) return cudaErrorInvalidValue;
-    static bool configured = false;
-    if (!configured) {
-        e = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OzSmem::TOTAL);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    const int64_t nkb = cdiv(K, OZ_TK);
-    const int kbs = (int)(cdiv(cdiv(nkb, OZ_CHUNK), splits) * OZ_CHUNK);  // whole chunks per split
-    splits = (int)cdiv(nkb, kbs);
-    dim3 grid((unsigned)cdiv(M, OZ_TM), (unsigned)cdiv(N, OZ_TN), (unsigned)splits);
-    k_oz_gemm<<<grid, OZ_THREADS, OzSmem::TOTAL, st>>>(ma, mb, (int)M, (int)N, (int)K, eA, eB, alpha, beta, C, ldc,
-                                                       kbs, P, status);
-    trace_count(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess || splits == 1) return e;
-    k_oz_reduce<<<oz_grid(M * N), 256, 0, st>>>((int)M, (int)N, splits, P, beta, C, ldc);
-    trace_count(1);
-    return cudaGetLastError();
+    p += oz_operand_bytes(M, K);
+    e = oz_split(!tb, B, ldb, N, K, p, &b, status, st);
+    if (e != cudaSuccess) return e;
+    p += oz_operand_bytes(N, K);
+    double* P = (double*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    const size_t used = (size_t)((char*)P - (char*)work);
+    return oz_product(a, 0, b, 0, M, N, alpha, beta, C, ldc, P, work_bytes > used ? work_bytes - used : 0, sms,
+                      status, st);
 }
 
 }  // namespace rutv

@@ -54,9 +54,11 @@ struct Workspace {
     float* qmodel;    // network parameters on the device
     void* oz;         // digit slices and exponents of the emulated FP64 products
     size_t oz_bytes;
+    void* oz_rows;    // digit planes of T(:, k0:n) split by rows (kept for one step)
+    void* oz_cols;    // digit planes of T22 split by columns (kept for one step)
 };
 
-constexpr int kSlots = 29;
+constexpr int kSlots = 31;
 struct Layout {
     size_t off[kSlots];
     size_t total;
@@ -120,7 +122,9 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec) {
         lp ? sizeof(unsigned long long) : 0,                        // max |T22|
         sizeof(float) * 32 + sizeof(double) * 4 * (size_t)wmax,     // learned-q features, q, candidates
         sizeof(float) * (size_t)learnq_nparam(),                    // learned-q model
-        emulated_prec(prec) ? oz_work_bytes(mx, std::max<int64_t>(wmax, 128), mx) : 0};  // Ozaki digits
+        emulated_prec(prec) ? oz_work_bytes(mx, std::max<int64_t>(wmax, 128), mx) : 0,   // Ozaki digits
+        emulated_prec(prec) ? oz_operand_bytes(m, n) : 0,                               // T(:, k0:n) by rows
+        emulated_prec(prec) ? oz_operand_bytes(n, m) : 0};                              // T22 by columns
     size_t o = 0;
     for (int i = 0; i < kSlots; ++i) {
         L.off[i] = o;
@@ -166,7 +170,9 @@ Workspace carve(void* base, const Layout& L) {
     w.dq = (double*)(p + L.off[26] + sizeof(float) * 32);
     w.qmodel = (float*)(p + L.off[27]);
     w.oz = (void*)(p + L.off[28]);
-    w.oz_bytes = L.total - L.off[28];
+    w.oz_bytes = L.off[29] - L.off[28];
+    w.oz_rows = L.off[30] > L.off[29] ? (void*)(p + L.off[29]) : nullptr;
+    w.oz_cols = L.total > L.off[30] ? (void*)(p + L.off[30]) : nullptr;
     return w;
 }
 
@@ -207,6 +213,15 @@ cudaError_t cached_workspace(int dev, size_t bytes, void** out) {
 
 enum SketchMode { MODE_FIXED = 0, MODE_LEARNED = 1, MODE_TRACE = 2 };
 
+// Splits of the trailing matrix reused by the emulated products of one block
+// step while T is unchanged: T(:, k0:n) by rows serves Z = T22 Y (rows k0:m)
+// and the right update's T(:, k0:n) W_V; T22 by columns serves Y = T22^T Z.
+struct OzCache {
+    int64_t k0 = -1;
+    bool rows = false, cols = false;
+    OzOperand r{}, c{};
+};
+
 struct Ctx {
     int64_t m, n, ldt;
     int b, q, prec;
@@ -220,6 +235,7 @@ struct Ctx {
     uint64_t seed;
     double *U, *T, *V;
     Workspace w;
+    OzCache oc;
     int sms;
     cudaStream_t st;
 };
@@ -233,6 +249,60 @@ cudaError_t gemm(Ctx& c, const char* role, bool ta, bool tb, int64_t M, int64_t 
         return oz_gemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.w.oz, c.w.oz_bytes, c.sms, c.w.status,
                        c.st);
     return gemm_f64(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.w.part, c.w.part_elems, c.sms, c.st);
+}
+
+bool oz_shape(const Ctx& c, int64_t M, int64_t N, int64_t K) {
+    return emulated_prec(c.prec) && c.w.oz_rows != nullptr && M >= 128 && N >= 64 && K >= 64;
+}
+
+const OzOperand* oz_rows_of(Ctx& c, int64_t k0, cudaError_t* e) {
+    if (c.oc.k0 != k0) c.oc = OzCache{k0};
+    if (!c.oc.rows) {
+        TraceScope ts("oz_split_cached", 0.0, 24.0 * (double)c.m * (c.n - k0), c.st);
+        *e = oz_split(false, c.T + k0 * c.ldt, c.ldt, c.m, c.n - k0, c.w.oz_rows, &c.oc.r, c.w.status, c.st);
+        c.oc.rows = (*e == cudaSuccess);
+    }
+    return &c.oc.r;
+}
+
+const OzOperand* oz_cols_of(Ctx& c, int64_t k0, cudaError_t* e) {
+    if (c.oc.k0 != k0) c.oc = OzCache{k0};
+    if (!c.oc.cols) {
+        TraceScope ts("oz_split_cached", 0.0, 24.0 * (double)(c.m - k0) * (c.n - k0), c.st);
+        *e = oz_split(true, c.T + k0 + k0 * c.ldt, c.ldt, c.n - k0, c.m - k0, c.w.oz_cols, &c.oc.c, c.w.status,
+                      c.st);
+        c.oc.cols = (*e == cudaSuccess);
+    }
+    return &c.oc.c;
+}
+
+// Y (M x w) = La(a0 : a0 + M, :) B with La a cached split and B (K x w,
+// column-major) split afresh.
+cudaError_t oz_cached_product(Ctx& c, const char* role, const OzOperand& a, int64_t a0, int64_t M, int w,
+                              const double* B, int64_t ldb, double* Y, int64_t ldy) {
+    const int64_t K = a.K;
+    TraceScope ts(role, 2.0 * (double)M * w * K, 8.0 * ((double)M * K + (double)K * w + (double)M * w), c.st);
+    char* p = (char*)c.w.oz;
+    OzOperand bo;
+    CK(oz_split(true, B, ldb, w, K, p, &bo, c.w.status, c.st));
+    p += oz_operand_bytes(w, K);
+    double* P = (double*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    const size_t used = (size_t)((char*)P - (char*)c.w.oz);
+    return oz_product(a, a0, bo, 0, M, w, 1.0, 0.0, Y, ldy, P, c.w.oz_bytes > used ? c.w.oz_bytes - used : 0, c.sms,
+                      c.w.status, c.st);
+}
+
+// Sketch product with the trailing matrix T22 = T(k0:m, k0:n):
+// Y = T22^T B (tr) or Y = T22 B; B is K x b.
+cudaError_t sketch_gemm(Ctx& c, bool tr, int64_t k0, const double* B, int64_t ldb, double* Y, int64_t ldy) {
+    const int64_t mp = c.m - k0, np = c.n - k0;
+    const int64_t M = tr ? np : mp, K = tr ? mp : np;
+    if (!oz_shape(c, M, c.b, K))
+        return gemm(c, "gemm_sketch", tr, false, M, c.b, K, 1.0, c.T + k0 + k0 * c.ldt, c.ldt, B, ldb, 0.0, Y, ldy);
+    cudaError_t e = cudaSuccess;
+    const OzOperand* a = tr ? oz_cols_of(c, k0, &e) : oz_rows_of(c, k0, &e);
+    CK(e);
+    return oz_cached_product(c, "gemm_sketch", *a, tr ? 0 : k0, M, c.b, B, ldb, Y, ldy);
 }
 
 // Householder QR of a len x w panel plus its W (explicit) and Tf.
@@ -256,6 +326,24 @@ cudaError_t apply_right(Ctx& c, double* C, int64_t ldc, int64_t rows, int64_t co
     CK(gemm(c, "gemm_right", false, false, rows, w, cols, 1.0, C, ldc, c.w.W, cols, 0.0, c.w.X, rows));
     CK(gemm(c, "gemm_right_tf", false, false, rows, w, w, 1.0, c.w.X, rows, c.w.Tf, w, 0.0, c.w.X2, rows));
     return gemm(c, "gemm_right", false, true, rows, cols, w, -1.0, c.w.X2, rows, c.w.W, cols, 1.0, C, ldc);
+}
+
+// T(:, k0:n) := T(:, k0:n) (I - W Tf W^T) with the first product taken from
+// the cached row split of T(:, k0:n); T changes, so the cache is dropped.
+cudaError_t apply_right_T(Ctx& c, int64_t k0, int w) {
+    const int64_t rows = c.m, cols = c.n - k0;
+    double* C = c.T + k0 * c.ldt;
+    if (!oz_shape(c, rows, w, cols)) {
+        c.oc = OzCache{};
+        return apply_right(c, C, c.ldt, rows, cols, w);
+    }
+    cudaError_t e = cudaSuccess;
+    const OzOperand* a = oz_rows_of(c, k0, &e);
+    CK(e);
+    CK(oz_cached_product(c, "gemm_right", *a, 0, rows, w, c.w.W, cols, c.w.X, rows));
+    c.oc = OzCache{};
+    CK(gemm(c, "gemm_right_tf", false, false, rows, w, w, 1.0, c.w.X, rows, c.w.Tf, w, 0.0, c.w.X2, rows));
+    return gemm(c, "gemm_right", false, true, rows, cols, w, -1.0, c.w.X2, rows, c.w.W, cols, 1.0, C, c.ldt);
 }
 
 // C (len x cols) := (I - W Tf W^T)^T C, W = c.w.W (len x w).
@@ -365,21 +453,22 @@ cudaError_t lowp_iterate(Ctx& c, const LowpShape& s, int iters) {
 
 cudaError_t lowp_finish(Ctx& c, const LowpShape& s) { return f32_to_f64(c.w.Xf, s.np * c.b, c.w.Y, c.st); }
 
-// FP64 sketch: Y0 = T22^T G into c.w.Y; iterate: Y := T22^T (T22 Y).
-cudaError_t fp64_begin(Ctx& c, int64_t i, const double* T22, int64_t mp, int64_t np) {
-    const int b = c.b;
+// FP64 sketch of T22 = T(k0:m, k0:n): Y0 = T22^T G into c.w.Y; iterate:
+// Y := T22^T (T22 Y).
+cudaError_t fp64_begin(Ctx& c, int64_t i, int64_t k0) {
+    const int64_t mp = c.m - k0, np = c.n - k0;
     {
-        TraceScope ts("gaussian", 0.0, 8.0 * (double)mp * b, c.st);
-        CK(gaussian_f64(c.seed, i, mp, b, c.w.G, mp, c.st));
+        TraceScope ts("gaussian", 0.0, 8.0 * (double)mp * c.b, c.st);
+        CK(gaussian_f64(c.seed, i, mp, c.b, c.w.G, mp, c.st));
     }
-    return gemm(c, "gemm_sketch", true, false, np, b, mp, 1.0, T22, c.ldt, c.w.G, mp, 0.0, c.w.Y, np);
+    return sketch_gemm(c, true, k0, c.w.G, mp, c.w.Y, np);
 }
 
-cudaError_t fp64_iterate(Ctx& c, const double* T22, int64_t mp, int64_t np, double* Y, int iters) {
-    const int b = c.b;
+cudaError_t fp64_iterate(Ctx& c, int64_t k0, double* Y, int iters) {
+    const int64_t mp = c.m - k0, np = c.n - k0;
     for (int it = 0; it < iters; ++it) {
-        CK(gemm(c, "gemm_sketch", false, false, mp, b, np, 1.0, T22, c.ldt, Y, np, 0.0, c.w.Z, mp));
-        CK(gemm(c, "gemm_sketch", true, false, np, b, mp, 1.0, T22, c.ldt, c.w.Z, mp, 0.0, Y, np));
+        CK(sketch_gemm(c, false, k0, Y, np, c.w.Z, mp));
+        CK(sketch_gemm(c, true, k0, c.w.Z, mp, Y, np));
     }
     return cudaSuccess;
 }
@@ -395,12 +484,13 @@ cudaError_t block_features(Ctx& c, int64_t k0, int64_t np) {
 // Trace mode: diagonal the step would produce with q = 0..3, i.e. the
 // singular values of T22 Q1(q), Q1(q) = orth((T22^T T22)^q Y0); the q = 2
 // sketch is left in c.w.Y for the step itself.
-cudaError_t trace_candidates(Ctx& c, const double* T22, int64_t mp, int64_t np) {
+cudaError_t trace_candidates(Ctx& c, int64_t k0) {
+    const int64_t mp = c.m - k0, np = c.n - k0;
     const int b = c.b;
     double* Yc = c.w.tmp;
     CK(copy_matrix(c.w.Y, np, Yc, np, np, b, c.st));
     for (int q = 0; q < 4; ++q) {
-        if (q > 0) CK(fp64_iterate(c, T22, mp, np, Yc, 1));
+        if (q > 0) CK(fp64_iterate(c, k0, Yc, 1));
         if (q == 2) CK(copy_matrix(Yc, np, c.w.Y, np, np, b, c.st));
         // explicit Q1 of the Householder QR of Yc
         CK(copy_matrix(Yc, np, c.w.X2, np, np, b, c.st));
@@ -409,7 +499,7 @@ cudaError_t trace_candidates(Ctx& c, const double* T22, int64_t mp, int64_t np) 
         CK(gemm(c, "learnq_trace", false, true, b, b, b, 1.0, c.w.Tf, b, c.w.W, np, 0.0, c.w.G, b));
         CK(gemm(c, "learnq_trace", false, false, np, b, b, -1.0, c.w.W, np, c.w.G, b, 1.0, c.w.X, np));
         // sigma(T22 Q1) from the R of its QR
-        CK(gemm(c, "learnq_trace", false, false, mp, b, np, 1.0, T22, c.ldt, c.w.X, np, 0.0, c.w.Z, mp));
+        CK(sketch_gemm(c, false, k0, c.w.X, np, c.w.Z, mp));
         CK(panel_qr(c.w.Z, mp, mp, b, c.w.tau, c.w.pscr, c.w.bars, c.w.status, c.sms, c.st));
         CK(jacobi_svd(c.w.Z, mp, b, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status,
                       kMaxSweeps, c.st));
@@ -435,13 +525,13 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
             CK(lowp_iterate(c, ls, iters));
             CK(lowp_finish(c, ls));
         } else {
-            CK(fp64_begin(c, i, T22, mp, np));
-            CK(fp64_iterate(c, T22, mp, np, c.w.Y, iters));
+            CK(fp64_begin(c, i, k0));
+            CK(fp64_iterate(c, k0, c.w.Y, iters));
         }
     } else if (c.mode == MODE_TRACE) {
-        CK(fp64_begin(c, i, T22, mp, np));
+        CK(fp64_begin(c, i, k0));
         CK(block_features(c, k0, np));
-        CK(trace_candidates(c, T22, mp, np));
+        CK(trace_candidates(c, k0));
         if (c.tr_count < c.tr_max) {
             double cand[4 * 512];
             CK(cudaMemcpyAsync(c.tr_feat + 16 * c.tr_count, c.w.feat, sizeof(float) * 16, cudaMemcpyDeviceToHost,
@@ -473,7 +563,7 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
             CK(lowp_begin(c, i, T22, ls));
             CK(lowp_finish(c, ls));
         } else {
-            CK(fp64_begin(c, i, T22, mp, np));
+            CK(fp64_begin(c, i, k0));
         }
         CK(block_features(c, k0, np));
         int qh = c.q;
@@ -486,11 +576,11 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
             CK(lowp_iterate(c, ls, iters));
             CK(lowp_finish(c, ls));
         } else {
-            CK(fp64_iterate(c, T22, mp, np, c.w.Y, iters));
+            CK(fp64_iterate(c, k0, c.w.Y, iters));
         }
     }
     CK(factor_panel(c, c.w.Y, np, np, b));
-    CK(apply_right(c, c.T + k0 * ldt, ldt, m, np, b));
+    CK(apply_right_T(c, k0, b));
     if (c.V) CK(apply_right(c, c.V + k0 * n, n, n, np, b));
     return panel_and_svd(c, k0, b);
 }

@@ -51,3 +51,26 @@ def test_emulated_parity(rutv, m, n, b, q, kind, seed, prec_name):
         assert np.abs(T - To).max() <= 1e-10 * nrm
         assert np.abs(U @ T - Uo @ To).max() <= 1e-10 * nrm
         assert np.abs(T @ V.T - To @ Vo.T).max() <= 1e-10 * nrm
+
+
+@pytest.mark.parametrize("prec_name", ["RANDUTV_FP64_EMULATED", "RANDUTV_EMULATED_SKETCH_BF16"])
+def test_emulated_wide_updates(rutv, prec_name):
+    """Trailing updates large enough (over 600 tiles of 128 x 64) for the
+    32-column, two-CTAs-per-SM product; ragged in both dimensions. Two block
+    steps of the factorization, checked against two steps of the oracle."""
+    prec = getattr(rutv, prec_name)
+    m, n, b, q, seed, steps = 4000, 3000, 128, 1, 4, 2
+    A = synthetic.test_matrix(m, n, "geometric10", 31, 32)
+    U, T, V = rutv.factor(dev(A), b, q, seed, prec=prec, stop_after=steps)
+    torch.cuda.synchronize()
+    U, T, V = host(U), host(T), host(V)
+    nrm = np.linalg.norm(A)
+    assert np.linalg.norm(A - U @ T @ V.T) / nrm <= utv_bound(n)
+    assert np.linalg.norm(U.T @ U - np.eye(m)) <= utv_bound(m)
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= utv_bound(n)
+    assert np.array_equal(np.tril(T[:, :b * steps], -1), np.zeros((m, b * steps)))
+    if prec == rutv.RANDUTV_FP64_EMULATED:
+        Uo, To, Vo, _ = oracle.randutv(A, b, q, seed, stop_after=steps)
+        assert np.abs(T - To).max() <= 1e-10 * nrm
+        assert np.abs(U @ T - Uo @ To).max() <= 1e-10 * nrm
+        assert np.abs(T @ V.T - To @ Vo.T).max() <= 1e-10 * nrm
