@@ -12,11 +12,11 @@
 // With S = 8 digits (56 bits) and the digit pairs s + t <= S + 1 kept, the
 // error is about K 2^{-56} max|op(A)(r,:)| max|op(B)(:,c)| (digit truncation;
 // the dropped pairs weigh 2^{-70}).  One tcgen05 accumulator per digit sum d
-// lives in TMEM (8 x TN FP32 columns: all 512 for TN = 64, 256 for the
-// TN = 32 tiles of short-K products, two CTAs per SM); every 128 of K the partial
-// sums are exact integers in FP32 (<= 8 pairs x 128 x 127^2 < 2^24), and they
-// are folded into double-float (hi, lo) FP32 registers with exact
-// power-of-two weights.  The final value gets one FP64 epilogue per element.
+// lives in TMEM (8 x 32 FP32 columns per 128 x 32 output tile, two buffers);
+// every 128 of K the partial sums are exact integers in FP32 (<= 8 pairs x
+// 128 x 127^2 < 2^24), and they are folded into double-float (hi, lo) FP32
+// registers with exact power-of-two weights.  The final value gets one FP64
+// epilogue per element.
 //
 // Splitting works on the FP64 bit pattern with integer instructions only
 // (GB300's FP64 pipe would make a floating-point split cost more than the
@@ -39,10 +39,8 @@ namespace {
 
 constexpr int OZ_S = 8;         // digits per operand
 constexpr int OZ_TM = 128;      // output rows per CTA (UMMA M)
-constexpr int OZ_TN = 64;       // output columns per CTA (UMMA N); 32 for short-K products
 constexpr int OZ_TK = 64;       // K per stage (128 bytes of BF16)
 constexpr int OZ_CHUNK = 2;     // k-blocks per exact FP32 chunk (K = 128)
-constexpr int OZ_THREADS = 192; // warps 0-3 drain TMEM, warp 4 = TMA, warp 5 = MMA
 constexpr long long kOzWait = 1LL << 24;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -189,14 +187,30 @@ __global__ void k_oz_split(const double* __restrict__ X, int64_t ld, int R, int 
 }
 
 // ---------------------------------------------------------------- product
-template <int TN>
-struct OzSmem {
-    static constexpr int A_BYTES = OZ_TM * OZ_TK * 2;           // 16 KB
-    static constexpr int B_BYTES = TN * OZ_TK * 2;              // 8 KB (TN = 64)
-    static constexpr int B_SET = OZ_S * B_BYTES;                // 64 KB (TN = 64)
-    static constexpr int TOTAL = 2 * A_BYTES + 2 * B_SET + 1024 + 256;
-    static constexpr uint32_t TMEM_COLS = OZ_S * TN;            // 512 or 256
-};
+// Persistent kernel, one CTA per SM.  A job is one 128 x 32 output tile over
+// one K range (a split-K slice); jobs are dealt round-robin and consecutive
+// job ids are neighbouring column tiles, so CTAs running together share the
+// A digit tiles in L2.
+//   warp 8    : TMA producer (ring of OZ_AST A digit tiles, ring of OZ_BST
+//               stacked B digit sets)
+//   warp 9    : MMA issuer
+//   warps 0-7 : drain TMEM into double-float registers, then the epilogue
+// The 8 B digit planes of a k-block are stacked in shared memory (plane t =
+// rows 32t .. 32t+31 of one 256-row operand), so all pairs (s, t), t <= 7-s,
+// of A digit s are ONE MMA of N = 32 (8 - s) writing accumulator columns
+// 32s .. 255, whose column block d then holds the digit sum d = s + t.  Two
+// 256-column accumulator buffers alternate per 128-deep chunk: the drain of
+// one chunk overlaps the MMAs of the next.
+constexpr int OZ_TN = 32;                               // output columns per job
+constexpr int OZ_AST = 8;                               // A ring stages
+constexpr int OZ_BST = 2;                               // B ring stages
+constexpr int OZ_EPI = 8;                               // drain / epilogue warps
+constexpr int OZ_THREADS = (OZ_EPI + 2) * 32;
+constexpr int OZ_A_BYTES = OZ_TM * OZ_TK * 2;           // 16 KB
+constexpr int OZ_BPLANE = OZ_TN * OZ_TK * 2;            // 4 KB
+constexpr int OZ_B_BYTES = OZ_S * OZ_BPLANE;            // 32 KB
+constexpr int OZ_ACC = OZ_S * OZ_TN;                    // 256 TMEM columns per buffer
+constexpr int OZ_SMEM = OZ_AST * OZ_A_BYTES + OZ_BST * OZ_B_BYTES + 1024 + 256;
 
 // FP32 value x times 2^sh, built as an FP64 bit pattern with integer
 // instructions (exact); zero and FP32 subnormals give 0; returns false when
@@ -212,53 +226,60 @@ __device__ __forceinline__ bool f32_to_f64_scaled(float x, int sh, double& out) 
     return true;
 }
 
-template <int TN, int MINB>
-__global__ void __launch_bounds__(OZ_THREADS, MINB) k_oz_gemm(const __grid_constant__ CUtensorMap mapA,
-                                                           const __grid_constant__ CUtensorMap mapB, int M, int N,
-                                                           int K, const int* __restrict__ eA,
-                                                           const int* __restrict__ eB, double alpha, double beta,
-                                                           double* __restrict__ C, int64_t ldc, int kbs,
-                                                           double* __restrict__ P, int* status, int a_plane,
-                                                           int a_row0, int b_plane, int b_row0) {
-    using L = OzSmem<TN>;
+struct OzJobs {
+    int tiles_m, tiles_n, kbs, nkb_all, njobs;
+    __device__ __forceinline__ void get(int j, int& m0, int& n0, int& z, int& kb0, int& nkb) const {
+        const int tn = j % tiles_n, rest = j / tiles_n;
+        m0 = (rest % tiles_m) * OZ_TM;
+        n0 = tn * OZ_TN;
+        z = rest / tiles_m;
+        kb0 = z * kbs;
+        nkb = min(nkb_all, kb0 + kbs) - kb0;
+    }
+};
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant__ CUtensorMap mapA,
+                                                            const __grid_constant__ CUtensorMap mapB, int M, int N,
+                                                            const int* __restrict__ eA, const int* __restrict__ eB,
+                                                            double alpha, double beta, double* __restrict__ C,
+                                                            int64_t ldc, OzJobs jb, double* __restrict__ P,
+                                                            int* status, int a_plane, int a_row0, int b_plane,
+                                                            int b_row0) {
     extern __shared__ __align__(1024) uint8_t oz_raw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)oz_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* Abuf = sm;                               // 2 x A_BYTES
-    uint8_t* Bbuf = sm + 2 * L::A_BYTES;              // 2 x B_SET
-    uint64_t* bars = (uint64_t*)(sm + 2 * L::A_BYTES + 2 * L::B_SET);
-    uint64_t* a_full = bars;       // [2]
-    uint64_t* a_empty = bars + 2;  // [2]
-    uint64_t* b_full = bars + 4;   // [2]
-    uint64_t* b_empty = bars + 6;  // [2]
-    uint64_t* c_full = bars + 8;   // chunk accumulated
-    uint64_t* c_free = bars + 9;   // chunk drained
-    uint32_t* tslot = (uint32_t*)(bars + 10);
+    uint8_t* Abuf = sm;                                   // OZ_AST x 16 KB
+    uint8_t* Bbuf = sm + OZ_AST * OZ_A_BYTES;             // OZ_BST x 32 KB
+    uint64_t* bars = (uint64_t*)(Bbuf + OZ_BST * OZ_B_BYTES);
+    uint64_t* a_full = bars;                   // [OZ_AST]
+    uint64_t* a_empty = a_full + OZ_AST;       // [OZ_AST]
+    uint64_t* b_full = a_empty + OZ_AST;       // [OZ_BST]
+    uint64_t* b_empty = b_full + OZ_BST;       // [OZ_BST]
+    uint64_t* acc_full = b_empty + OZ_BST;     // [2] chunk accumulated
+    uint64_t* acc_empty = acc_full + 2;        // [2] chunk drained
+    uint32_t* tslot = (uint32_t*)(acc_empty + 2);
     __shared__ volatile int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * OZ_TM, n0 = blockIdx.y * TN;
-    // split z covers k-blocks [kb0, kb0 + nkb); gridDim.z > 1 writes FP64 partials to P
-    const int nkb_all = (K + OZ_TK - 1) / OZ_TK;
-    const int kb0 = blockIdx.z * kbs;
-    const int nkb = max(0, min(nkb_all, kb0 + kbs) - kb0);
-    const int nchunks = (nkb + OZ_CHUNK - 1) / OZ_CHUNK;
-    const bool partial = gridDim.z > 1;
-
+    const bool partial = jb.njobs > jb.tiles_m * jb.tiles_n;  // split-K: FP64 partials to P
     if (tid == 0) {
         s_abort = 0;
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < OZ_AST; ++i) {
             bar_init(&a_full[i], 1);
             bar_init(&a_empty[i], 1);
+        }
+        for (int i = 0; i < OZ_BST; ++i) {
             bar_init(&b_full[i], 1);
             bar_init(&b_empty[i], 1);
         }
-        bar_init(c_full, 1);
-        bar_init(c_free, 128);
+        for (int i = 0; i < 2; ++i) {
+            bar_init(&acc_full[i], 1);
+            bar_init(&acc_empty[i], OZ_EPI);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
-                     "r"(L::TMEM_COLS)
+                     "r"(2u * OZ_ACC)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -267,148 +288,172 @@ __global__ void __launch_bounds__(OZ_THREADS, MINB) k_oz_gemm(const __grid_const
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
 
-    if (warp == 4) {
-        if (lane == 0 && nkb > 0) {  // ---------------- TMA producer
-            int ia = 0, kb_done = 0;
-            for (int kb = 0; kb < nkb && !s_abort; ++kb) {
-                kb_done = kb + 1;
-                const int sb = kb & 1;
-                if (!bar_wait(&b_empty[sb], (uint32_t)(((kb >> 1) & 1) ^ 1))) { s_abort = 1; break; }
-                bar_expect(&b_full[sb], (uint32_t)L::B_SET);
-                for (int t = 0; t < OZ_S; ++t)
-                    tma2d(Bbuf + sb * L::B_SET + t * L::B_BYTES, &mapB, &b_full[sb], (kb0 + kb) * OZ_TK,
-                          t * b_plane + b_row0 + n0);
-                for (int s = 0; s < OZ_S; ++s, ++ia) {
-                    const int sa = ia & 1;
-                    if (!bar_wait(&a_empty[sa], (uint32_t)(((ia >> 1) & 1) ^ 1))) { s_abort = 1; break; }
-                    bar_expect(&a_full[sa], (uint32_t)L::A_BYTES);
-                    tma2d(Abuf + sa * L::A_BYTES, &mapA, &a_full[sa], (kb0 + kb) * OZ_TK, s * a_plane + a_row0 + m0);
+    if (warp == OZ_EPI) {
+        if (lane == 0) {  // ---------------- TMA producer
+            long long ia = 0, ib = 0;
+            for (int j = blockIdx.x; j < jb.njobs && !s_abort; j += gridDim.x) {
+                int m0, n0, z, kb0, nkb;
+                jb.get(j, m0, n0, z, kb0, nkb);
+                for (int kb = 0; kb < nkb && !s_abort; ++kb) {
+                    const int k = (kb0 + kb) * OZ_TK;
+                    const int sb = (int)(ib % OZ_BST);
+                    if (!bar_wait(&b_empty[sb], (uint32_t)(((ib / OZ_BST) & 1) ^ 1))) { s_abort = 1; break; }
+                    bar_expect(&b_full[sb], (uint32_t)OZ_B_BYTES);
+                    for (int t = 0; t < OZ_S; ++t)
+                        tma2d(Bbuf + sb * OZ_B_BYTES + t * OZ_BPLANE, &mapB, &b_full[sb], k, t * b_plane + b_row0 + n0);
+                    ++ib;
+                    for (int s = 0; s < OZ_S; ++s) {
+                        const int sa = (int)(ia % OZ_AST);
+                        if (!bar_wait(&a_empty[sa], (uint32_t)(((ia / OZ_AST) & 1) ^ 1))) { s_abort = 1; break; }
+                        bar_expect(&a_full[sa], (uint32_t)OZ_A_BYTES);
+                        tma2d(Abuf + sa * OZ_A_BYTES, &mapA, &a_full[sa], k, s * a_plane + a_row0 + m0);
+                        ++ia;
+                    }
                 }
             }
             // every copy issued must land before the CTA can exit
-            for (int kb = max(0, kb_done - 2); kb < kb_done; ++kb) bar_wait(&b_full[kb & 1], (uint32_t)((kb >> 1) & 1));
-            for (int i = max(0, ia - 2); i < ia; ++i) bar_wait(&a_full[i & 1], (uint32_t)((i >> 1) & 1));
+            for (long long i = (ib > OZ_BST ? ib - OZ_BST : 0); i < ib; ++i)
+                bar_wait(&b_full[i % OZ_BST], (uint32_t)((i / OZ_BST) & 1));
+            for (long long i = (ia > OZ_AST ? ia - OZ_AST : 0); i < ia; ++i)
+                bar_wait(&a_full[i % OZ_AST], (uint32_t)((i / OZ_AST) & 1));
         }
-    } else if (warp == 5) {
-        if (lane == 0 && nkb > 0) {  // ---------------- MMA issuer
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                                   ((uint32_t)(OZ_TM >> 4) << 24);
-            int ia = 0, chunk = 0;
-            for (int kb = 0; kb < nkb && !s_abort; ++kb) {
-                const int sb = kb & 1;
-                const bool first_of_chunk = (kb % OZ_CHUNK) == 0;
-                if (first_of_chunk && chunk > 0) {
-                    if (!bar_wait(c_free, (uint32_t)((chunk - 1) & 1))) { s_abort = 1; break; }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                }
-                if (!bar_wait(&b_full[sb], (uint32_t)((kb >> 1) & 1))) { s_abort = 1; break; }
-                for (int s = 0; s < OZ_S; ++s, ++ia) {
-                    const int sa = ia & 1;
-                    if (!bar_wait(&a_full[sa], (uint32_t)((ia >> 1) & 1))) { s_abort = 1; break; }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint64_t da = desc_sw128(su32(Abuf + sa * L::A_BYTES));
-                    for (int t = 0; t + s < OZ_S; ++t) {
-                        const uint64_t db = desc_sw128(su32(Bbuf + sb * L::B_SET + t * L::B_BYTES));
-                        const uint32_t dt = tmem + (uint32_t)((s + t) * TN);
+    } else if (warp == OZ_EPI + 1) {
+        if (lane == 0) {  // ---------------- MMA issuer
+            long long ia = 0, ib = 0, chunk = 0;
+            for (int j = blockIdx.x; j < jb.njobs && !s_abort; j += gridDim.x) {
+                int m0, n0, z, kb0, nkb;
+                jb.get(j, m0, n0, z, kb0, nkb);
+                for (int kb = 0; kb < nkb && !s_abort; ++kb) {
+                    const bool first = (kb % OZ_CHUNK) == 0;
+                    const uint32_t buf = (uint32_t)(chunk & 1);
+                    if (first) {
+                        if (!bar_wait(&acc_empty[buf], (uint32_t)(((chunk >> 1) & 1) ^ 1))) { s_abort = 1; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    }
+                    const int sb = (int)(ib % OZ_BST);
+                    if (!bar_wait(&b_full[sb], (uint32_t)((ib / OZ_BST) & 1))) { s_abort = 1; break; }
+                    const uint64_t db = desc_sw128(su32(Bbuf + sb * OZ_B_BYTES));
+                    for (int s = 0; s < OZ_S; ++s) {
+                        const int sa = (int)(ia % OZ_AST);
+                        if (!bar_wait(&a_full[sa], (uint32_t)((ia / OZ_AST) & 1))) { s_abort = 1; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint64_t da = desc_sw128(su32(Abuf + sa * OZ_A_BYTES));
+                        const uint32_t dt = tmem + buf * OZ_ACC + (uint32_t)(s * OZ_TN);
+                        // M = 128, N = 32 (8 - s), BF16 x BF16 -> FP32, both K-major
+                        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                               ((uint32_t)(((OZ_S - s) * OZ_TN) >> 3) << 17) |
+                                               ((uint32_t)(OZ_TM >> 4) << 24);
 #pragma unroll
                         for (int k = 0; k < OZ_TK / 16; ++k) {
                             const uint64_t ko = (uint64_t)((k * 32) >> 4);
-                            const uint32_t acc = (!first_of_chunk || s > 0 || k > 0) ? 1u : 0u;
+                            const uint32_t acc = (!first || s > 0 || k > 0) ? 1u : 0u;
                             asm volatile(
                                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
                                 "l"(da + ko), "l"(db + ko), "r"(idesc), "r"(acc)
                                 : "memory");
                         }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                         su32(&a_empty[sa]))
+                                     : "memory");
+                        ++ia;
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     su32(&a_empty[sa]))
+                                     su32(&b_empty[sb]))
                                  : "memory");
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 su32(&b_empty[sb]))
-                             : "memory");
-                if ((kb % OZ_CHUNK) == OZ_CHUNK - 1 || kb == nkb - 1) {
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     su32(c_full))
-                                 : "memory");
-                    ++chunk;
+                    ++ib;
+                    if ((kb % OZ_CHUNK) == OZ_CHUNK - 1 || kb == nkb - 1) {
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                         su32(&acc_full[buf]))
+                                     : "memory");
+                        ++chunk;
+                    }
                 }
             }
         }
-    } else {  // ---------------- warps 0-3: drain TMEM into double-float
-        float hi[TN], lo[TN];
+    } else {  // ---------------- warps 0-7: drain TMEM, epilogue
+        const int quad = warp & 3, half = warp >> 2;  // TMEM lanes 32 quad.., columns 16 half..
+        long long chunk = 0;
+        for (int j = blockIdx.x; j < jb.njobs; j += gridDim.x) {
+            int m0, n0, z, kb0, nkb;
+            jb.get(j, m0, n0, z, kb0, nkb);
+            float hi[16], lo[16];
 #pragma unroll
-        for (int j = 0; j < TN; ++j) hi[j] = lo[j] = 0.0f;
-        bool ok = true;
-        for (int ch = 0; ch < nchunks; ++ch) {
-            ok = __all_sync(0xffffffffu, bar_wait(c_full, (uint32_t)(ch & 1)));
-            if (!ok || s_abort) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0.0f;
+            const int nch = (nkb + OZ_CHUNK - 1) / OZ_CHUNK;
+            bool ok = true;
+            for (int ch = 0; ch < nch; ++ch, ++chunk) {
+                const uint32_t buf = (uint32_t)(chunk & 1);
+                ok = __all_sync(0xffffffffu, bar_wait(&acc_full[buf], (uint32_t)((chunk >> 1) & 1)));
+                if (!ok || s_abort) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-            for (int d = OZ_S - 1; d >= 0; --d) {
-                const float w = __int_as_float((127 - 7 * (d + 2)) << 23);  // 2^{-7(d+2)}
-#pragma unroll
-                for (int c0 = 0; c0 < TN; c0 += 32) {
-                    uint32_t v[32];
-                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TN + c0);
+                for (int d = OZ_S - 1; d >= 0; --d) {
+                    const float w = __int_as_float((127 - 7 * (d + 2)) << 23);  // 2^{-7(d+2)}
+                    uint32_t v[16];
+                    const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + buf * OZ_ACC +
+                                        (uint32_t)(d * OZ_TN + half * 16);
                     asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-                        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                        "%14,%15}, [%16];"
                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
-                          "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
-                          "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                          "=r"(v[14]), "=r"(v[15])
                         : "r"(ta));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
+                    for (int c = 0; c < 16; ++c) {
                         float s, e;
-                        two_sum(hi[c0 + j], __uint_as_float(v[j]) * w, s, e);
-                        hi[c0 + j] = s;
-                        lo[c0 + j] += e;
+                        two_sum(hi[c], __uint_as_float(v[c]) * w, s, e);
+                        hi[c] = s;
+                        lo[c] += e;
                     }
                 }
-            }
 #pragma unroll
-            for (int j = 0; j < TN; ++j) {  // renormalise (fast two-sum)
-                float s = hi[j] + lo[j];
-                lo[j] = lo[j] - (s - hi[j]);
-                hi[j] = s;
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            bar_arrive(c_free);
-        }
-        if (!ok && lane == 0) atomicOr(status, ST_TIMEOUT);
-        const int r = m0 + warp * 32 + lane;
-        double* Pz = partial ? P + (size_t)blockIdx.z * (size_t)M * (size_t)N : nullptr;
-        if (ok && !s_abort && r < M) {
-            const int er = eA[r];
-            // alpha = +-1 folds into the sign; beta in {0, 1} needs no multiply
-            const bool unit_alpha = (alpha == 1.0 || alpha == -1.0);
-            const unsigned long long sgn = (alpha < 0.0) ? (1ull << 63) : 0ull;
-#pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                const int c = n0 + j;
-                if (c >= N) break;
-                const int ec = eB[c];
-                double v = 0.0;
-                if (er != INT_MIN && ec != INT_MIN) {
-                    double dh, dl;
-                    if (unit_alpha && f32_to_f64_scaled(hi[j], er + ec, dh) && f32_to_f64_scaled(lo[j], er + ec, dl)) {
-                        v = __longlong_as_double(__double_as_longlong(dh) ^ (long long)sgn) +
-                            __longlong_as_double(__double_as_longlong(dl) ^ (long long)sgn);
-                    } else {  // general alpha or extreme exponents
-                        const double scale = ldexp(alpha, er + ec);
-                        v = fma((double)hi[j], scale, (double)lo[j] * scale);
-                    }
+                for (int c = 0; c < 16; ++c) {  // renormalise (fast two-sum)
+                    float s = hi[c] + lo[c];
+                    lo[c] = lo[c] - (s - hi[c]);
+                    hi[c] = s;
                 }
-                if (partial) {
-                    Pz[r + (size_t)c * M] = v;
-                } else {
-                    double* cp = C + r + (int64_t)c * ldc;
-                    *cp = (beta == 0.0) ? v : (beta == 1.0 ? *cp + v : fma(beta, *cp, v));
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) bar_arrive(&acc_empty[buf]);
+            }
+            if (!ok || s_abort) {
+                if (!ok && lane == 0) atomicOr(status, ST_TIMEOUT);
+                s_abort = 1;
+                break;
+            }
+            const int r = m0 + quad * 32 + lane;
+            if (r < M) {
+                const int er = eA[r];
+                // alpha = +-1 folds into the sign; beta in {0, 1} needs no multiply
+                const bool unit_alpha = (alpha == 1.0 || alpha == -1.0);
+                const long long sgn = (alpha < 0.0) ? (long long)(1ull << 63) : 0ll;
+                double* Pz = partial ? P + (size_t)z * (size_t)M * (size_t)N : nullptr;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int col = n0 + half * 16 + c;
+                    if (col >= N) break;
+                    const int ec = eB[col];
+                    double v = 0.0;
+                    if (er != INT_MIN && ec != INT_MIN) {
+                        double dh, dl;
+                        if (unit_alpha && f32_to_f64_scaled(hi[c], er + ec, dh) &&
+                            f32_to_f64_scaled(lo[c], er + ec, dl)) {
+                            v = __longlong_as_double(__double_as_longlong(dh) ^ sgn) +
+                                __longlong_as_double(__double_as_longlong(dl) ^ sgn);
+                        } else {  // general alpha or extreme exponents
+                            const double scale = ldexp(alpha, er + ec);
+                            v = fma((double)hi[c], scale, (double)lo[c] * scale);
+                        }
+                    }
+                    if (partial) {
+                        Pz[r + (size_t)col * M] = v;
+                    } else {
+                        double* cp = C + r + (int64_t)col * ldc;
+                        *cp = (beta == 0.0) ? v : (beta == 1.0 ? *cp + v : fma(beta, *cp, v));
+                    }
                 }
             }
         }
@@ -417,7 +462,7 @@ __global__ void __launch_bounds__(OZ_THREADS, MINB) k_oz_gemm(const __grid_const
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * OZ_ACC) : "memory");
 }
 
 // C = sum_z P[z] (fixed order) + beta C
@@ -463,23 +508,17 @@ unsigned oz_grid(int64_t total) { return (unsigned)std::max<int64_t>(1, std::min
 
 int64_t oz_ldq(int64_t K) { return (K + 63) / 64 * 64; }
 
-// short-K products with many output tiles (the rank-b updates) use 32-column
-// tiles: 256 TMEM columns and ~97 KB of shared memory let two CTAs share an
-// SM, so one's epilogue overlaps the other's MMAs
-int oz_tn(int64_t M, int64_t N, int64_t K, int sms) {
-    return (K <= 256 && cdiv(M, OZ_TM) * cdiv(N, 64) >= 4LL * sms) ? 32 : 64;
-}
-
-// split-K factor: slices of whole 128-deep chunks until the grid covers the
-// SMs about twice; partials (FP64) need splits * M * N doubles
-int oz_splits(int64_t M, int64_t N, int64_t K, int sms) {
-    const int64_t tiles = cdiv(M, OZ_TM) * cdiv(N, oz_tn(M, N, K, sms));
+// split-K factor: slices of whole 128-deep chunks until there are about
+// four jobs per SM; partials (FP64) need splits * M * N doubles
+int oz_splits(int64_t M, int64_t N, int64_t K, int sms, size_t p_bytes) {
+    const int64_t tiles = cdiv(M, OZ_TM) * cdiv(N, OZ_TN);
     const int64_t chunks = cdiv(cdiv(K, OZ_TK), OZ_CHUNK);
     int64_t s = 1;
-    if (tiles < 2LL * sms) s = cdiv(2LL * sms, tiles);
+    if (tiles < 4LL * sms) s = cdiv(4LL * sms, tiles);
     if (s > chunks) s = chunks;
     if (s > 64) s = 64;
-    if ((size_t)s * M * N > ((size_t)1 << 27)) s = 1;  // partials bounded at 1 GiB
+    const int64_t fit = (int64_t)(p_bytes / (sizeof(double) * (size_t)M * (size_t)N));
+    if (s > fit) s = fit;
     return (int)std::max<int64_t>(s, 1);
 }
 
@@ -520,36 +559,29 @@ cudaError_t oz_product(const OzOperand& a, int64_t a_row0, const OzOperand& b, i
     const int64_t K = a.K;
     if (b.K != K || a_row0 < 0 || b_row0 < 0 || a_row0 + M > a.R || b_row0 + N > b.R) return cudaErrorInvalidValue;
     if (M < OZ_TM || N < OZ_TN || K < OZ_TK) return cudaErrorInvalidValue;  // one TMA box at least
-    const int tn = oz_tn(M, N, K, sms);
-    int splits = oz_splits(M, N, K, sms);
-    if (sizeof(double) * (size_t)splits * M * N > p_bytes) splits = 1;
     CUtensorMap ma, mb;
     if (!oz_map(&ma, a.Q, (int64_t)OZ_S * a.plane, K, a.ldq, OZ_TM)) return cudaErrorInvalidValue;
-    if (!oz_map(&mb, b.Q, (int64_t)OZ_S * b.plane, K, b.ldq, tn)) return cudaErrorInvalidValue;
+    if (!oz_map(&mb, b.Q, (int64_t)OZ_S * b.plane, K, b.ldq, OZ_TN)) return cudaErrorInvalidValue;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_oz_gemm<64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             OzSmem<64>::TOTAL);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_oz_gemm<32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     OzSmem<32>::TOTAL);
+        cudaError_t e = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int64_t nkb = cdiv(K, OZ_TK);
-    const int kbs = (int)(cdiv(cdiv(nkb, OZ_CHUNK), splits) * OZ_CHUNK);  // whole chunks per split
-    splits = (int)cdiv(nkb, kbs);
-    dim3 grid((unsigned)cdiv(M, OZ_TM), (unsigned)cdiv(N, tn), (unsigned)splits);
-    const int* eA = a.e + a_row0;
-    const int* eB = b.e + b_row0;
-    if (tn == 32)
-        k_oz_gemm<32, 2><<<grid, OZ_THREADS, OzSmem<32>::TOTAL, st>>>(
-            ma, mb, (int)M, (int)N, (int)K, eA, eB, alpha, beta, C, ldc, kbs, P, status, (int)a.plane, (int)a_row0,
-            (int)b.plane, (int)b_row0);
-    else
-        k_oz_gemm<64, 1><<<grid, OZ_THREADS, OzSmem<64>::TOTAL, st>>>(
-            ma, mb, (int)M, (int)N, (int)K, eA, eB, alpha, beta, C, ldc, kbs, P, status, (int)a.plane, (int)a_row0,
-            (int)b.plane, (int)b_row0);
+    OzJobs jb;
+    jb.tiles_m = (int)cdiv(M, OZ_TM);
+    jb.tiles_n = (int)cdiv(N, OZ_TN);
+    jb.nkb_all = (int)cdiv(K, OZ_TK);
+    const int s0 = oz_splits(M, N, K, sms, p_bytes);
+    jb.kbs = (int)(cdiv(cdiv(jb.nkb_all, OZ_CHUNK), s0) * OZ_CHUNK);  // whole chunks per split
+    const int splits = (int)cdiv(jb.nkb_all, jb.kbs);
+    const int64_t njobs = (int64_t)jb.tiles_m * jb.tiles_n * splits;
+    if (njobs > INT_MAX) return cudaErrorInvalidValue;
+    jb.njobs = (int)njobs;
+    const unsigned grid = (unsigned)std::min<int64_t>(njobs, sms);
+    k_oz_gemm<<<grid, OZ_THREADS, OZ_SMEM, st>>>(ma, mb, (int)M, (int)N, a.e + a_row0, b.e + b_row0, alpha, beta, C,
+                                                   ldc, jb, P, status, (int)a.plane, (int)a_row0, (int)b.plane,
+                                                   (int)b_row0);
     trace_count(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || splits == 1) return e;
