@@ -120,13 +120,14 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
         const bool act = s_scalars[3] != 0.0;
         for (int c = j + 1 + tid; c < w; c += PNT) wv[c] = act ? (__ldcg(pv + c) + sred[c] / d) : 0.0;
 
-        // (a) v_r = x_r / d on own rows r > j; P(j,j) = beta
+        // (a) v_r = x_r / d on own rows r > j; P(j,j) = beta; xc keeps tau_j v_r
         if (act) {
+            const double rd = 1.0 / d;
             for (int t = tid; t < nr; t += PNT) {
                 int r = r0 + t;
                 if (r > j) {
-                    double v = xc[t] / d;
-                    xc[t] = v;
+                    double v = xc[t] * rd;
+                    xc[t] = tj * v;
                     PX(t, j) = v;
                 }
             }
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
                 double* e = &PX(t, j + 1);
                 val = *e;
                 if (act) {
-                    val -= tj * xc[t] * wv[j + 1];
+                    val = fma(-xc[t], wv[j + 1], val);
                     *e = val;
                 }
             }
@@ -167,10 +168,10 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
                         double* e = &PX(t, c);
                         double val = *e;
                         if (act) {
-                            val -= tj * xc[t] * wc;
+                            val = fma(-xc[t], wc, val);
                             *e = val;
                         }
-                        acc += xn[t] * val;
+                        acc = fma(xn[t], val, acc);
                     }
                 }
             }
@@ -237,6 +238,40 @@ __global__ void k_tfactor(const double* __restrict__ gram, const double* __restr
     }
 }
 
+// Same triangular factor, one block (one warp) per column j and the
+// substitution written column-oriented: once Tf(k, j) is known, lane i adds
+// (W^T W)(i, k) Tf(k, j) to its running sum for every row i < k, and
+// Tf(k-1, j) = -tau_{k-1} sum(k-1) is then complete.  Every step is one FMA
+// per lane and a warp-level exchange, so the w-long dependent chain costs
+// about w short steps instead of w dot products; the block's triangle of
+// the Gram matrix is staged in shared memory (w <= 128), packed: column k
+// (rows 0..k-1) at offset k (k - 1) / 2.
+constexpr int TF_MAXW = 128;
+__global__ void __launch_bounds__(32) k_tfactor_col(const double* __restrict__ gram, const double* __restrict__ tau,
+                                                    int w, double* __restrict__ Tf, int* status) {
+    extern __shared__ double gs[];
+    __shared__ double acc[TF_MAXW];
+    const int j = blockIdx.x, lane = threadIdx.x;
+    for (int k = 1; k <= j; ++k)
+        for (int i = lane; i < k; i += 32) gs[k * (k - 1) / 2 + i] = gram[i + (size_t)k * w];
+    for (int i = lane; i < j; i += 32) acc[i] = 0.0;
+    double* x = Tf + (size_t)j * w;
+    for (int i = j + 1 + lane; i < w; i += 32) x[i] = 0.0;
+    const double tj = tau[j];
+    if (lane == 0) {
+        if (!isfinite(tj)) atomicOr(status, ST_NONFINITE);
+        x[j] = tj;
+    }
+    __syncwarp();
+    double xk = tj;
+    for (int k = j; k >= 1; --k) {
+        for (int i = lane; i < k; i += 32) acc[i] = fma(gs[k * (k - 1) / 2 + i], xk, acc[i]);
+        __syncwarp();
+        xk = -tau[k - 1] * acc[k - 1];
+        if (lane == 0) x[k - 1] = xk;
+    }
+}
+
 }  // namespace
 
 int panel_qr_grid(int64_t len, int w, int sms) {
@@ -296,6 +331,18 @@ cudaError_t tfactor(const double* gram, const double* tau, int w, double* Tf, in
         cudaError_t e = cudaFuncSetAttribute(k_tfactor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;
         configured = shm;
+    }
+    if (w <= TF_MAXW) {
+        const size_t tri = sizeof(double) * (size_t)w * (w - 1) / 2;
+        static thread_local size_t configured_col = 0;
+        if (tri > 48 * 1024 && tri > configured_col) {
+            cudaError_t e = cudaFuncSetAttribute(k_tfactor_col, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri);
+            if (e != cudaSuccess) return e;
+            configured_col = tri;
+        }
+        k_tfactor_col<<<w, 32, tri, st>>>(gram, tau, w, Tf, status);
+        trace_count(1);
+        return cudaGetLastError();
     }
     const int threads = std::min(1024, ((w + 31) / 32) * 32);
     k_tfactor<<<1, threads, shm, st>>>(gram, tau, w, Tf, use_smem, status);

@@ -16,10 +16,11 @@
 // GB300 design: FP64 runs at ~7 GFLOP/s per SM, so a single block would need
 // tens of milliseconds for b = 128.  The w/2 disjoint pairs of every round of
 // a round-robin ("circle") ordering are spread over many SMs instead:
-//   - k_jacobi_cluster (default): one 8-block thread-block cluster; A and V
-//     live in the blocks' shared memory, each warp rotates one pair per round
-//     through distributed shared memory, the hardware cluster barrier
-//     separates rounds;
+//   - k_jacobi_cluster (default): one thread-block cluster of 16 blocks (8
+//     where 16 cannot be scheduled); A and V live in the blocks' shared
+//     memory, eight lanes rotate one pair through distributed shared memory
+//     (a warp serves four pairs with each FP64 instruction), the hardware
+//     cluster barrier separates rounds;
 //   - k_jacobi: w/2 blocks of one cooperative launch, one pair per block, A
 //     and V in an L2-resident global scratch, a software grid barrier between
 //     rounds (used when the cluster's shared memory is too small, and by the
@@ -27,6 +28,9 @@
 // The pair order differs from a cyclic-by-rows sweep, which changes only
 // rounding: the converged, canonical SVD is the same.
 #include <cooperative_groups.h>
+
+#include <mutex>
+#include <unordered_map>
 
 #include "common.cuh"
 #include "internal.h"
@@ -200,17 +204,23 @@ __global__ void __launch_bounds__(NT) k_jacobi(const double* __restrict__ R, int
 
 
 // ---------------------------------------------------------------------------
-// Cluster variant: one thread-block cluster of JC_CTAS blocks.  Column c of
-// the working copies A and V lives in the shared memory of block
-// c / cols_per_block; every round each warp rotates one pair (p, q) of the
-// circle ordering through distributed shared memory (its lanes own rows), and
-// the hardware cluster barrier separates rounds.  Same schedule, rotation and
-// canonical output as k_jacobi; only the order of the three dot-product sums
-// differs (rounding).
-constexpr int JC_CTAS = 8;
-constexpr int JC_THREADS = 256;
+// Cluster variant: one thread-block cluster of G blocks (G = 16 or 8, set at
+// launch).  Column c of the working copies A and V lives in the shared memory
+// of block c / cols_per_block.  Each round, eight lanes take one pair (p, q)
+// of the circle ordering, the rows split over the lanes, and read and write
+// the columns through distributed shared memory; a warp serves four pairs.
+// GB300 issues FP64 at about two lanes per clock per SM, so the work per
+// round is spread over one warp in each block, the rotation is computed by
+// the eight lanes of its pair only, with one square root, one division and
+// one reciprocal square root; the hardware cluster barrier separates rounds.
+// Same schedule, test and canonical output as k_jacobi; the rotation is the
+// same up to rounding: with d = beta - alpha and g = 2 gamma,
+// t = sign(d / g) |g| / (|d| + sqrt(d^2 + g^2)) equals
+// sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) for zeta = d / g.
+constexpr int JC_THREADS = 128;
+constexpr int JC_LPP = 8;  // lanes per pair
 
-__global__ void __cluster_dims__(JC_CTAS, 1, 1) __launch_bounds__(JC_THREADS)
+__global__ void __launch_bounds__(JC_THREADS)
     k_jacobi_cluster(const double* __restrict__ R, int64_t ldr, int w, int n2, int cpb, double* __restrict__ D,
                      double* __restrict__ Us, double* __restrict__ Vs, int* status, int max_sweeps, double tol) {
     cg::cluster_group cluster = cg::this_cluster();
@@ -219,9 +229,14 @@ __global__ void __cluster_dims__(JC_CTAS, 1, 1) __launch_bounds__(JC_THREADS)
     double* Vloc = jsm + (size_t)cpb * w;     // cpb columns x w
     double* nrm = Vloc + (size_t)cpb * w;     // cpb norms
     __shared__ int s_flag;
+    const int G = (int)cluster.num_blocks();
     const int me = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int NWALL = JC_CTAS * (JC_THREADS / 32);
+    const int sub = lane & (JC_LPP - 1);
+    const int PPW = 32 / JC_LPP;                     // pairs per warp
+    const int NWALL = G * (JC_THREADS / 32);
+    const int npairs = n2 / 2;
+    const double tol2 = tol * tol;
 
     for (int lc = 0; lc < cpb; ++lc) {
         const int c = me * cpb + lc;
@@ -243,48 +258,73 @@ __global__ void __cluster_dims__(JC_CTAS, 1, 1) __launch_bounds__(JC_THREADS)
         if (tid == 0) s_flag = 0;
         cluster.sync();
         for (int round = 0; round < n2 - 1; ++round) {
-            for (int k = me * (JC_THREADS / 32) + warp; k < n2 / 2; k += NWALL) {
-                int p = circle_elem(k, round, n2);
-                int q = circle_elem(n2 - 1 - k, round, n2);
-                if (p > q) { int t = p; p = q; q = t; }
-                if (q >= w) continue;
-                double* ap = colA(p);
-                double* aq = colA(q);
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int r = lane; r < w; r += 32) {
-                    double x = ap[r], y = aq[r];
-                    al += x * x;
-                    be += y * y;
-                    ga += x * y;
+            // global warp index: warp 0 of every block first
+            for (int gw = warp * G + me; gw * PPW < npairs; gw += NWALL) {
+                const int k = gw * PPW + lane / JC_LPP;
+                int p = 0, q = 0;
+                bool act = k < npairs;
+                if (act) {
+                    p = circle_elem(k, round, n2);
+                    q = circle_elem(n2 - 1 - k, round, n2);
+                    if (p > q) { int t = p; p = q; q = t; }
+                    act = q < w;
                 }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
+                double* ap = act ? colA(p) : nullptr;
+                double* aq = act ? colA(q) : nullptr;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                if (act)
+                    for (int r = sub; r < w; r += JC_LPP) {
+                        const double x = ap[r], y = aq[r];
+                        al = fma(x, x, al);
+                        be = fma(y, y, be);
+                        ga = fma(x, y, ga);
+                    }
+#pragma unroll
+                for (int o = JC_LPP / 2; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                }
+                if (!act) continue;
                 if (!isfinite(al) || !isfinite(be) || !isfinite(ga)) {
-                    if (lane == 0) atomicOr(status, ST_NONFINITE);
+                    if (sub == 0) atomicOr(status, ST_NONFINITE);
                     continue;
                 }
-                if (ga == 0.0 || fabs(ga) <= tol * sqrt(al * be)) continue;
-                double zeta = (be - al) / (2.0 * ga);
-                double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                double cs = 1.0 / sqrt(1.0 + t * t);
-                double sn = cs * t;
+                // |gamma| > tol sqrt(alpha beta), squared where that cannot under- or overflow
+                const double pr = al * be;
+                bool rot;
+                if (ga == 0.0) rot = false;
+                else if (pr > 1e-290 && pr < 1e290) rot = ga * ga > tol2 * pr;
+                else rot = fabs(ga) > tol * sqrt(al) * sqrt(be);
+                if (!rot) continue;
+                const double d = be - al, g = 2.0 * ga;
+                const double ad = fabs(d), ag = fabs(g);
+                double t;
+                if (ad < 1e150 && ag < 1e150 && ag > 1e-150) {
+                    const double sg = (d == 0.0 || ((d > 0.0) == (g > 0.0))) ? 1.0 : -1.0;
+                    t = sg * ag / (ad + sqrt(fma(d, d, g * g)));
+                } else {
+                    const double zeta = d / g;
+                    t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                }
+                const double cs = rsqrt(fma(t, t, 1.0));
+                const double sn = cs * t;
                 double* vp = colV(p);
                 double* vq = colV(q);
-                for (int r = lane; r < w; r += 32) {
-                    double x = ap[r], y = aq[r];
+                for (int r = sub; r < w; r += JC_LPP) {
+                    const double x = ap[r], y = aq[r];
                     ap[r] = cs * x - sn * y;
                     aq[r] = sn * x + cs * y;
-                    double u = vp[r], z = vq[r];
+                    const double u = vp[r], z = vq[r];
                     vp[r] = cs * u - sn * z;
                     vq[r] = sn * u + cs * z;
                 }
-                if (lane == 0) s_flag = 1;
+                if (sub == 0) s_flag = 1;
             }
             cluster.sync();
         }
         int any = 0;
-        for (int b = 0; b < JC_CTAS; ++b) any |= *cluster.map_shared_rank(&s_flag, b);
+        for (int b = 0; b < G; ++b) any |= *cluster.map_shared_rank(&s_flag, b);
         converged = (any == 0);
         cluster.sync();  // every block has read the flags before they are reset
     }
@@ -357,6 +397,42 @@ __global__ void __cluster_dims__(JC_CTAS, 1, 1) __launch_bounds__(JC_THREADS)
     }
 }
 
+// Largest cluster (16, else 8) of k_jacobi_cluster the current device can
+// schedule with the biggest shared-memory request; 0 when neither fits.
+int jacobi_cluster_blocks() {
+    static std::mutex mu;
+    static std::unordered_map<int, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int best = 0;
+    if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
+    for (int g : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)g);
+        cfg.blockDim = dim3(JC_THREADS);
+        cfg.dynamicSmemBytes = 48 * 1024;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)g;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_jacobi_cluster, &cfg) == cudaSuccess && n > 0) {
+            best = g;
+            break;
+        }
+        cudaGetLastError();
+    }
+    cache[dev] = best;
+    return best;
+}
+
 }  // namespace
 
 size_t jacobi_scratch_elems(int w) { return (size_t)2 * w * w; }
@@ -368,20 +444,33 @@ cudaError_t jacobi_svd(const double* R, int64_t ldr, int w, double* D, double* U
     int n2 = w + (w & 1);
     double tol = (double)w * 1.1102230246251565e-16;
     // cluster variant when A and V fit in the cluster's shared memory
-    const int cpb = (n2 + JC_CTAS - 1) / JC_CTAS;
-    const size_t shm_cluster = sizeof(double) * ((size_t)2 * cpb * w + cpb);
-    if (allow_cluster && shm_cluster <= 200 * 1024) {
-        static thread_local size_t configured = 0;
-        if (shm_cluster > 48 * 1024 && shm_cluster > configured) {
-            cudaError_t e =
-                cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_cluster);
-            if (e != cudaSuccess) return e;
-            configured = shm_cluster;
+    const int gcl = jacobi_cluster_blocks();
+    if (allow_cluster && gcl > 0) {
+        const int cpb = (n2 + gcl - 1) / gcl;
+        const size_t shm_cluster = sizeof(double) * ((size_t)2 * cpb * w + cpb);
+        if (shm_cluster <= 200 * 1024) {
+            static thread_local size_t configured = 0;
+            if (shm_cluster > 48 * 1024 && shm_cluster > configured) {
+                cudaError_t e = cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)shm_cluster);
+                if (e != cudaSuccess) return e;
+                configured = shm_cluster;
+            }
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)gcl);
+            cfg.blockDim = dim3(JC_THREADS);
+            cfg.dynamicSmemBytes = shm_cluster;
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)gcl;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            trace_count(1);
+            return cudaLaunchKernelEx(&cfg, k_jacobi_cluster, R, ldr, w, n2, cpb, D, Us, Vs, status, max_sweeps, tol);
         }
-        trace_count(1);
-        k_jacobi_cluster<<<JC_CTAS, JC_THREADS, shm_cluster, st>>>(R, ldr, w, n2, cpb, D, Us, Vs, status, max_sweeps,
-                                                                    tol);
-        return cudaGetLastError();
     }
     int G = std::max(1, n2 / 2);
     double* A = scratch;
