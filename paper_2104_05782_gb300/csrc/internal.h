@@ -37,9 +37,17 @@ cudaError_t tfactor(const double* gram, const double* tau, int w, double* Tf, in
 size_t jacobi_scratch_elems(int w);
 // SVD of the upper triangle of R (w x w, ldr): D (w), Us, Vs (w x w, ld w).
 // allow_cluster = false forces the grid variant that works in `scratch`.
+// dense: use all of R (not only its upper triangle); V0 (w x w, ld w, or
+// null for I): starting V, so that Vs = V0 W for the rotations W applied.
 cudaError_t jacobi_svd(const double* R, int64_t ldr, int w, double* D, double* Us, double* Vs,
                        double* scratch, unsigned* bar, int* counters, int* status, int max_sweeps,
-                       cudaStream_t st, bool allow_cluster = true);
+                       cudaStream_t st, bool allow_cluster = true, bool dense = false,
+                       const double* V0 = nullptr);
+// FP32 Jacobi on the upper triangle of R (w <= 128): its accumulated right
+// rotations, orthogonal to FP32 accuracy, as FP64 Q0 (w x w, ld w).
+cudaError_t jacobi32_precondition(const double* R, int64_t ldr, int w, double* Q0, int max_sweeps, cudaStream_t st);
+// U (w x w, ld w) := upper triangle of R.
+cudaError_t triu_copy(const double* R, int64_t ldr, int w, double* U, cudaStream_t st);
 
 // ---- element-wise kernels (misc.cu) ---------------------------------------
 cudaError_t gaussian_f64(uint64_t seed, int64_t step, int64_t rows, int64_t cols, double* G, int64_t ldg,

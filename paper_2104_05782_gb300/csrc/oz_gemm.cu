@@ -91,13 +91,19 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // ---------------------------------------------------------------- splitting
-// Exponent E+1 of a nonzero finite double (|x| < 2^{E+1}); 0-exponent values
-// (zero, subnormal) give INT_MIN so they never set the row scale.
-__device__ __forceinline__ int exp_of(double x) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    const int be = (int)((bits >> 52) & 0x7FF);
-    return be == 0 ? INT_MIN : be - 1022;
+// Everything here is integer or FP32 work: on GB300 one FP64 instruction
+// (even a compare) costs a warp 64 clocks of its SM sub-partition's FP64
+// unit, and the int-to-float conversions run at a quarter of the ALU rate.
+//
+// Biased exponent field of a double: 0 for zero / subnormal, 2047 for
+// Inf / NaN.
+__device__ __forceinline__ int bexp_of(double x) {
+    return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
 }
+
+// row scale from the largest biased exponent of the row: |x| < 2^(be - 1022);
+// rows of zeros / subnormals give INT_MIN so they never set a scale
+__device__ __forceinline__ int scale_of(int maxbe) { return maxbe == 0 ? INT_MIN : maxbe - 1022; }
 
 // row maxima of the exponent: L(r, k) = trans ? X(k, r) : X(r, k)
 __global__ void k_oz_rowexp(const double* __restrict__ X, int64_t ld, int R, int K, bool trans, int* __restrict__ e,
@@ -105,42 +111,37 @@ __global__ void k_oz_rowexp(const double* __restrict__ X, int64_t ld, int R, int
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (trans) {  // row r = column r of X: contiguous, one warp per row
         for (int r = blockIdx.x * 8 + warp; r < R; r += gridDim.x * 8) {
-            int m = INT_MIN;
-            bool bad = false;
-            for (int k = lane; k < K; k += 32) {
-                double v = X[k + (int64_t)r * ld];
-                bad |= !isfinite(v);
-                m = max(m, exp_of(v));
-            }
+            int m = 0;
+            for (int k = lane; k < K; k += 32) m = max(m, bexp_of(X[k + (int64_t)r * ld]));
             for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE);
-            if (lane == 0) e[r] = m;
+            if (lane == 0) {
+                if (m == 0x7FF) atomicOr(status, ST_NONFINITE);
+                e[r] = scale_of(m);
+            }
         }
     } else {  // row r strided: 32 rows per block, lanes over rows, warps over k
         __shared__ int sm[8][33];
         const int r0 = blockIdx.x * 32;
         const int r = r0 + lane;
-        int m = INT_MIN;
-        bool bad = false;
+        int m = 0;
         if (r < R)
-            for (int k = warp; k < K; k += 8) {
-                double v = X[r + (int64_t)k * ld];
-                bad |= !isfinite(v);
-                m = max(m, exp_of(v));
-            }
-        if (bad) atomicOr(status, ST_NONFINITE);
+            for (int k = warp; k < K; k += 8) m = max(m, bexp_of(X[r + (int64_t)k * ld]));
         sm[warp][lane] = m;
         __syncthreads();
         if (warp == 0 && r < R) {
             int mm = sm[0][lane];
             for (int w = 1; w < 8; ++w) mm = max(mm, sm[w][lane]);
-            e[r] = mm;
+            if (mm == 0x7FF) atomicOr(status, ST_NONFINITE);
+            e[r] = scale_of(mm);
         }
     }
 }
 
-// digits: Q[s][r][k] (s < OZ_S, row stride ldq, slice stride R*ldq) in BF16
-__device__ __forceinline__ void split_one(double x, int er, uint16_t* out, size_t slice_stride) {
+// digits of x against the row scale er: F = floor(|x| 2^(7S - er)) < 2^56,
+// digit s = bits 7(S-1-s) .. 7(S-1-s)+6 of F, signed like x.  BF16 of a
+// magnitude a < 2^7 without a conversion instruction: the float with bits
+// 0x4B000000 | a is 2^23 + a, and subtracting 2^23 leaves a exactly.
+__device__ __forceinline__ void digits_of(double x, int er, uint32_t* dg) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const int be = (int)((bits >> 52) & 0x7FF);
     unsigned long long F = 0ull;
@@ -151,26 +152,38 @@ __device__ __forceinline__ void split_one(double x, int er, uint16_t* out, size_
         if (sh >= 0) F = mant << sh;  // F < 2^{7S} <= 2^56 since |x| < 2^er
         else if (sh > -64) F = mant >> (-sh);
     }
-    const bool neg = (bits >> 63) != 0;
+    const uint32_t sgn = (uint32_t)(bits >> 63) << 15;
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
-        int digit = (int)((F >> (7 * (OZ_S - 1 - s))) & 127ull);
-        float f = (float)(neg ? -digit : digit);
-        __nv_bfloat16 h = __float2bfloat16_rn(f);
-        out[(size_t)s * slice_stride] = *reinterpret_cast<uint16_t*>(&h);
+        const uint32_t a = (uint32_t)(F >> (7 * (OZ_S - 1 - s))) & 127u;
+        const float f = __int_as_float((int)(0x4B000000u | a)) - 8388608.0f;
+        dg[s] = (__float_as_uint(f) >> 16) | sgn;
     }
 }
 
+// digits: Q[s][r][k] (s < OZ_S, row stride ldq, slice stride R*ldq) in BF16.
+// trans: L(r, k) = X(k, r), four consecutive k per thread (one 8-byte store
+// per digit plane); else a 32 x 32 tile is transposed through shared memory.
+// Columns K..ldq-1 of Q are never read (the tensor map ends at K).
 __global__ void k_oz_split(const double* __restrict__ X, int64_t ld, int R, int K, bool trans,
                            const int* __restrict__ e, uint16_t* __restrict__ Q, int64_t ldq) {
     const size_t slice = (size_t)R * ldq;
-    if (trans) {  // L(r, k) = X(k, r): k contiguous in memory and in Q
-        const int64_t total = (int64_t)R * K;
+    if (trans) {
+        const int64_t kq = (K + 3) / 4;
+        const int64_t total = (int64_t)R * kq;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-            const int k = (int)(i % K), r = (int)(i / K);
-            split_one(X[k + (int64_t)r * ld], e[r], Q + (size_t)r * ldq + k, slice);
+            const int k = (int)(i % kq) * 4, r = (int)(i / kq);
+            const int er = e[r];
+            uint32_t dg[4][OZ_S];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) digits_of(k + u < K ? X[k + u + (int64_t)r * ld] : 0.0, er, dg[u]);
+            uint16_t* q = Q + (size_t)r * ldq + k;
+#pragma unroll
+            for (int s = 0; s < OZ_S; ++s)
+                *reinterpret_cast<uint2*>(q + (size_t)s * slice) =
+                    make_uint2(dg[0][s] | (dg[1][s] << 16), dg[2][s] | (dg[3][s] << 16));
         }
-    } else {  // L(r, k) = X(r, k): transpose through a 32 x 32 tile
+    } else {
         __shared__ double tile[32][33];
         const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
         const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
@@ -180,8 +193,14 @@ __global__ void k_oz_split(const double* __restrict__ X, int64_t ld, int R, int 
         }
         __syncthreads();
         for (int j = ty; j < 32; j += 8) {
-            int r = r0 + j, k = k0 + tx;
-            if (r < R && k < K) split_one(tile[tx][j], e[r], Q + (size_t)r * ldq + k, slice);
+            const int r = r0 + j, k = k0 + tx;
+            if (r < R && k < K) {
+                uint32_t dg[OZ_S];
+                digits_of(tile[tx][j], e[r], dg);
+                uint16_t* q = Q + (size_t)r * ldq + k;
+#pragma unroll
+                for (int s = 0; s < OZ_S; ++s) q[(size_t)s * slice] = (uint16_t)dg[s];
+            }
         }
     }
 }
@@ -244,7 +263,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                                                             double alpha, double beta, double* __restrict__ C,
                                                             int64_t ldc, OzJobs jb, double* __restrict__ P,
                                                             int* status, int a_plane, int a_row0, int b_plane,
-                                                            int b_row0) {
+                                                            int b_row0, int amode, int bmode) {
     extern __shared__ __align__(1024) uint8_t oz_raw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)oz_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* Abuf = sm;                                   // OZ_AST x 16 KB
@@ -387,26 +406,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                 ok = __all_sync(0xffffffffu, bar_wait(&acc_full[buf], (uint32_t)((chunk >> 1) & 1)));
                 if (!ok || s_abort) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + buf * OZ_ACC + (uint32_t)(half * 16);
 #pragma unroll 1
-                for (int d = OZ_S - 1; d >= 0; --d) {
-                    const float w = __int_as_float((127 - 7 * (d + 2)) << 23);  // 2^{-7(d+2)}
-                    uint32_t v[16];
-                    const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + buf * OZ_ACC +
-                                        (uint32_t)(d * OZ_TN + half * 16);
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-                        "%14,%15}, [%16];"
-                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                          "=r"(v[14]), "=r"(v[15])
-                        : "r"(ta));
+                for (int g = 1; g >= 0; --g) {  // digit sums 7..4, then 3..0: four loads, one wait
+                    uint32_t v[4][16];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint32_t ta = tbase + (uint32_t)((4 * g + 3 - i) * OZ_TN);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+                            "%13,%14,%15}, [%16];"
+                            : "=r"(v[i][0]), "=r"(v[i][1]), "=r"(v[i][2]), "=r"(v[i][3]), "=r"(v[i][4]),
+                              "=r"(v[i][5]), "=r"(v[i][6]), "=r"(v[i][7]), "=r"(v[i][8]), "=r"(v[i][9]),
+                              "=r"(v[i][10]), "=r"(v[i][11]), "=r"(v[i][12]), "=r"(v[i][13]), "=r"(v[i][14]),
+                              "=r"(v[i][15])
+                            : "r"(ta));
+                    }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        float s, e;
-                        two_sum(hi[c], __uint_as_float(v[c]) * w, s, e);
-                        hi[c] = s;
-                        lo[c] += e;
+                    for (int i = 0; i < 4; ++i) {
+                        const int d = 4 * g + 3 - i;
+                        const float w = __int_as_float((127 - 7 * (d + 2)) << 23);  // 2^{-7(d+2)}
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            float s, e;
+                            two_sum(hi[c], __uint_as_float(v[i][c]) * w, s, e);
+                            hi[c] = s;
+                            lo[c] += e;
+                        }
                     }
                 }
 #pragma unroll
@@ -425,34 +452,41 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                 break;
             }
             const int r = m0 + quad * 32 + lane;
-            if (r < M) {
+            const int cb = n0 + half * 16;
+            const int ncols = min(16, N - cb);
+            if (r < M && ncols > 0) {
                 const int er = eA[r];
-                // alpha = +-1 folds into the sign; beta in {0, 1} needs no multiply
-                const bool unit_alpha = (alpha == 1.0 || alpha == -1.0);
-                const long long sgn = (alpha < 0.0) ? (long long)(1ull << 63) : 0ll;
+                int ec[16];
+                double cv[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) ec[c] = (c < ncols) ? eB[cb + c] : INT_MIN;
+                if (!partial && bmode != 0) {  // all loads of C in flight at once
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) cv[c] = (c < ncols) ? C[r + (int64_t)(cb + c) * ldc] : 0.0;
+                }
+                // amode: 1 alpha = +1, 2 alpha = -1 (folded into the sign), 0 general
+                const long long sgn = (amode == 2) ? (long long)(1ull << 63) : 0ll;
                 double* Pz = partial ? P + (size_t)z * (size_t)M * (size_t)N : nullptr;
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
-                    const int col = n0 + half * 16 + c;
-                    if (col >= N) break;
-                    const int ec = eB[col];
+                    if (c >= ncols) continue;
                     double v = 0.0;
-                    if (er != INT_MIN && ec != INT_MIN) {
+                    if (er != INT_MIN && ec[c] != INT_MIN) {
                         double dh, dl;
-                        if (unit_alpha && f32_to_f64_scaled(hi[c], er + ec, dh) &&
-                            f32_to_f64_scaled(lo[c], er + ec, dl)) {
+                        if (amode != 0 && f32_to_f64_scaled(hi[c], er + ec[c], dh) &&
+                            f32_to_f64_scaled(lo[c], er + ec[c], dl)) {
                             v = __longlong_as_double(__double_as_longlong(dh) ^ sgn) +
                                 __longlong_as_double(__double_as_longlong(dl) ^ sgn);
                         } else {  // general alpha or extreme exponents
-                            const double scale = ldexp(alpha, er + ec);
+                            const double scale = ldexp(alpha, er + ec[c]);
                             v = fma((double)hi[c], scale, (double)lo[c] * scale);
                         }
                     }
                     if (partial) {
-                        Pz[r + (size_t)col * M] = v;
+                        Pz[r + (size_t)(cb + c) * M] = v;
                     } else {
-                        double* cp = C + r + (int64_t)col * ldc;
-                        *cp = (beta == 0.0) ? v : (beta == 1.0 ? *cp + v : fma(beta, *cp, v));
+                        // bmode: 0 beta = 0, 1 beta = 1, 2 general
+                        C[r + (int64_t)(cb + c) * ldc] = (bmode == 0) ? v : (bmode == 1 ? cv[c] + v : fma(beta, cv[c], v));
                     }
                 }
             }
@@ -466,14 +500,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
 }
 
 // C = sum_z P[z] (fixed order) + beta C
-__global__ void k_oz_reduce(int M, int N, int S, const double* __restrict__ P, double beta, double* __restrict__ C,
-                            int64_t ldc) {
+__global__ void k_oz_reduce(int M, int N, int S, const double* __restrict__ P, double beta, int bzero,
+                            double* __restrict__ C, int64_t ldc) {
     const int64_t total = (int64_t)M * N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int z = 0; z < S; ++z) s += P[(size_t)z * total + e];
         double* c = C + (e % M) + (e / M) * ldc;
-        *c = (beta == 0.0) ? s : fma(beta, *c, s);
+        *c = bzero ? s : fma(beta, *c, s);
     }
 }
 
@@ -542,7 +576,7 @@ cudaError_t oz_split(bool trans, const double* X, int64_t ldx, int64_t R, int64_
     if (trans) {
         k_oz_rowexp<<<(unsigned)std::min<int64_t>(cdiv(R, 8), 4096), 256, 0, st>>>(X, ldx, (int)R, (int)K, true, e,
                                                                                       status);
-        k_oz_split<<<oz_grid(R * K), 256, 0, st>>>(X, ldx, (int)R, (int)K, true, e, Q, ldq);
+        k_oz_split<<<oz_grid(R * cdiv(K, 4)), 256, 0, st>>>(X, ldx, (int)R, (int)K, true, e, Q, ldq);
     } else {
         k_oz_rowexp<<<(unsigned)cdiv(R, 32), 256, 0, st>>>(X, ldx, (int)R, (int)K, false, e, status);
         k_oz_split<<<dim3((unsigned)cdiv(R, 32), (unsigned)cdiv(K, 32)), 256, 0, st>>>(X, ldx, (int)R, (int)K, false,
@@ -579,13 +613,15 @@ cudaError_t oz_product(const OzOperand& a, int64_t a_row0, const OzOperand& b, i
     if (njobs > INT_MAX) return cudaErrorInvalidValue;
     jb.njobs = (int)njobs;
     const unsigned grid = (unsigned)std::min<int64_t>(njobs, sms);
+    const int amode = (alpha == 1.0) ? 1 : (alpha == -1.0 ? 2 : 0);
+    const int bmode = (beta == 0.0) ? 0 : (beta == 1.0 ? 1 : 2);
     k_oz_gemm<<<grid, OZ_THREADS, OZ_SMEM, st>>>(ma, mb, (int)M, (int)N, a.e + a_row0, b.e + b_row0, alpha, beta, C,
                                                    ldc, jb, P, status, (int)a.plane, (int)a_row0, (int)b.plane,
-                                                   (int)b_row0);
+                                                   (int)b_row0, amode, bmode);
     trace_count(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || splits == 1) return e;
-    k_oz_reduce<<<oz_grid(M * N), 256, 0, st>>>((int)M, (int)N, splits, P, beta, C, ldc);
+    k_oz_reduce<<<oz_grid(M * N), 256, 0, st>>>((int)M, (int)N, splits, P, beta, beta == 0.0 ? 1 : 0, C, ldc);
     trace_count(1);
     return cudaGetLastError();
 }

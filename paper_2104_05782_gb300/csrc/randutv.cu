@@ -21,6 +21,7 @@
 #include <mutex>
 #include <new>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "../../include/randutv.h"
@@ -56,9 +57,10 @@ struct Workspace {
     size_t oz_bytes;
     void* oz_rows;    // digit planes of T(:, k0:n) split by rows (kept for one step)
     void* oz_cols;    // digit planes of T22 split by columns (kept for one step)
+    double* svdp;     // FP32-preconditioned SVD: Q, Q', Gram, triu(R), R Q (w x w each), or null
 };
 
-constexpr int kSlots = 31;
+constexpr int kSlots = 32;
 struct Layout {
     size_t off[kSlots];
     size_t total;
@@ -66,6 +68,9 @@ struct Layout {
 };
 
 int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+// widths whose b x b SVD takes the FP32-preconditioned route
+bool svd_precond_width(int w) { return w >= 64 && w <= 128; }
 
 bool lowp_prec(int prec) {
     return prec == RANDUTV_SKETCH_BF16 || prec == RANDUTV_SKETCH_FP16_SCALED || prec == RANDUTV_EMULATED_SKETCH_BF16;
@@ -124,7 +129,8 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec) {
         sizeof(float) * (size_t)learnq_nparam(),                    // learned-q model
         emulated_prec(prec) ? oz_work_bytes(mx, std::max<int64_t>(wmax, 128), mx) : 0,   // Ozaki digits
         emulated_prec(prec) ? oz_operand_bytes(m, n) : 0,                               // T(:, k0:n) by rows
-        emulated_prec(prec) ? oz_operand_bytes(n, m) : 0};                              // T22 by columns
+        emulated_prec(prec) ? oz_operand_bytes(n, m) : 0,                               // T22 by columns
+        svd_precond_width((int)wmax) ? sizeof(double) * 5 * (size_t)wmax * wmax : 0};  // preconditioned SVD
     size_t o = 0;
     for (int i = 0; i < kSlots; ++i) {
         L.off[i] = o;
@@ -172,7 +178,8 @@ Workspace carve(void* base, const Layout& L) {
     w.oz = (void*)(p + L.off[28]);
     w.oz_bytes = L.off[29] - L.off[28];
     w.oz_rows = L.off[30] > L.off[29] ? (void*)(p + L.off[29]) : nullptr;
-    w.oz_cols = L.total > L.off[30] ? (void*)(p + L.off[30]) : nullptr;
+    w.oz_cols = L.off[31] > L.off[30] ? (void*)(p + L.off[30]) : nullptr;
+    w.svdp = L.total > L.off[31] ? (double*)(p + L.off[31]) : nullptr;
     return w;
 }
 
@@ -354,6 +361,35 @@ cudaError_t apply_left_t(Ctx& c, double* C, int64_t ldc, int64_t len, int64_t co
     return gemm(c, "gemm_left", false, false, len, cols, w, -1.0, c.w.W, len, c.w.X2, w, 1.0, C, ldc);
 }
 
+// SVD of the w x w upper triangle of R (Sec. 3.2.3).  For 64 <= w <= 128 the
+// FP64 Jacobi is preconditioned: an FP32 Jacobi gives Q (orthogonal to about
+// 1e-6), two Newton-Schulz steps Q := Q (3I - Q^T Q) / 2 make it orthogonal
+// to FP64 rounding, and the FP64 Jacobi then runs on R Q with V starting at
+// Q, so Vs = Q W and R = Us diag(D) Vs^T as before, after a few sweeps.
+cudaError_t svd_block(Ctx& c, const double* R, int64_t ldr, int w) {
+    TraceScope tsv("jacobi_svd", 0.0, 8.0 * 3.0 * (double)w * w, c.st);
+    if (!c.w.svdp || !svd_precond_width(w))
+        return jacobi_svd(R, ldr, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status,
+                          kMaxSweeps, c.st);
+    const size_t w2 = (size_t)w * w;
+    double* Q = c.w.svdp;
+    double* Q1 = Q + w2;
+    double* G = Q1 + w2;
+    double* Ru = G + w2;
+    double* X = Ru + w2;
+    CK(jacobi32_precondition(R, ldr, w, Q, 12, c.st));
+    for (int it = 0; it < 2; ++it) {
+        CK(gemm(c, "svd_precond", true, false, w, w, w, 1.0, Q, w, Q, w, 0.0, G, w));
+        CK(copy_matrix(Q, w, Q1, w, w, w, c.st));
+        CK(gemm(c, "svd_precond", false, false, w, w, w, -0.5, Q, w, G, w, 1.5, Q1, w));
+        std::swap(Q, Q1);
+    }
+    CK(triu_copy(R, ldr, w, Ru, c.st));
+    CK(gemm(c, "svd_precond", false, false, w, w, w, 1.0, Ru, w, Q, w, 0.0, X, w));
+    return jacobi_svd(X, w, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status, kMaxSweeps,
+                      c.st, true, true, Q);
+}
+
 // Panel QR of T(k0:m, k0:k0+w), left update, small SVD and its application.
 cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
     const int64_t m = c.m, n = c.n, ldt = c.ldt;
@@ -363,11 +399,7 @@ cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
     CK(factor_panel(c, P, ldt, mp, w));
     CK(apply_left_t(c, T + k0 + (k0 + w) * ldt, ldt, mp, n - k0 - w, w));
     if (c.U) CK(apply_right(c, c.U + k0 * m, m, m, mp, w));
-    {
-        TraceScope tsv("jacobi_svd", 0.0, 8.0 * 3.0 * (double)w * w, c.st);
-        CK(jacobi_svd(P, ldt, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status,
-                      kMaxSweeps, c.st));
-    }
+    CK(svd_block(c, P, ldt, w));
     if (k0 > 0) {  // T(0:k0, blk) := T(0:k0, blk) Vs
         CK(gemm(c, "gemm_svdapply", false, false, k0, w, w, 1.0, T + k0 * ldt, ldt, c.w.Vs, w, 0.0, c.w.tmp, k0));
         CK(copy_matrix(c.w.tmp, k0, T + k0 * ldt, ldt, k0, w, c.st));

@@ -18,9 +18,8 @@
 // a round-robin ("circle") ordering are spread over many SMs instead:
 //   - k_jacobi_cluster (default): one thread-block cluster of 16 blocks (8
 //     where 16 cannot be scheduled); A and V live in the blocks' shared
-//     memory, eight lanes rotate one pair through distributed shared memory
-//     (a warp serves four pairs with each FP64 instruction), the hardware
-//     cluster barrier separates rounds;
+//     memory, one warp rotates one pair through distributed shared memory,
+//     the hardware cluster barrier separates rounds;
 //   - k_jacobi: w/2 blocks of one cooperative launch, one pair per block, A
 //     and V in an L2-resident global scratch, a software grid barrier between
 //     rounds (used when the cluster's shared memory is too small, and by the
@@ -72,17 +71,18 @@ __global__ void __launch_bounds__(NT) k_jacobi(const double* __restrict__ R, int
                                                double* __restrict__ A, double* __restrict__ V,
                                                double* __restrict__ D, double* __restrict__ Us,
                                                double* __restrict__ Vs, unsigned* bar, int* rot, int* status,
-                                               int max_sweeps, double tol) {
+                                               int max_sweeps, double tol, int dense,
+                                               const double* __restrict__ V0) {
     __shared__ double red[3 * (NT / 32)];
     __shared__ int s_flag;
     const int tid = threadIdx.x, G = gridDim.x, cta = blockIdx.x;
     unsigned target = 0;
 
-    // A := upper triangle of R, V := I (ld w)
+    // A := upper triangle of R (all of R when dense), V := V0 or I (ld w)
     for (int c = cta; c < w; c += G)
         for (int r = tid; r < w; r += NT) {
-            A[r + (size_t)c * w] = (r <= c) ? R[r + (int64_t)c * ldr] : 0.0;
-            V[r + (size_t)c * w] = (r == c) ? 1.0 : 0.0;
+            A[r + (size_t)c * w] = (dense || r <= c) ? R[r + (int64_t)c * ldr] : 0.0;
+            V[r + (size_t)c * w] = V0 ? V0[r + (size_t)c * w] : ((r == c) ? 1.0 : 0.0);
         }
     if (cta == 0 && tid < 3) rot[tid] = 0;
     if (!grid_sync(bar, target, status)) return;
@@ -206,23 +206,25 @@ __global__ void __launch_bounds__(NT) k_jacobi(const double* __restrict__ R, int
 // ---------------------------------------------------------------------------
 // Cluster variant: one thread-block cluster of G blocks (G = 16 or 8, set at
 // launch).  Column c of the working copies A and V lives in the shared memory
-// of block c / cols_per_block.  Each round, eight lanes take one pair (p, q)
-// of the circle ordering, the rows split over the lanes, and read and write
-// the columns through distributed shared memory; a warp serves four pairs.
-// GB300 issues FP64 at about two lanes per clock per SM, so the work per
-// round is spread over one warp in each block, the rotation is computed by
-// the eight lanes of its pair only, with one square root, one division and
-// one reciprocal square root; the hardware cluster barrier separates rounds.
+// of block c / cols_per_block.  Each round, the lanes of one warp take one
+// pair (p, q) of the circle ordering, the rows split over the lanes, and read
+// and write the columns through distributed shared memory.  GB300's FP64
+// unit retires about one warp instruction per 64 clocks per SM sub-partition,
+// so the w/2 pairs of a round go to w/2 different warps (four per block, one
+// per sub-partition), and the rotation takes one square root, one division
+// and one reciprocal square root; the hardware cluster barrier separates
+// rounds.
 // Same schedule, test and canonical output as k_jacobi; the rotation is the
 // same up to rounding: with d = beta - alpha and g = 2 gamma,
 // t = sign(d / g) |g| / (|d| + sqrt(d^2 + g^2)) equals
 // sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) for zeta = d / g.
 constexpr int JC_THREADS = 128;
-constexpr int JC_LPP = 8;  // lanes per pair
+constexpr int JC_LPP = 32;  // lanes per pair
 
 __global__ void __launch_bounds__(JC_THREADS)
     k_jacobi_cluster(const double* __restrict__ R, int64_t ldr, int w, int n2, int cpb, double* __restrict__ D,
-                     double* __restrict__ Us, double* __restrict__ Vs, int* status, int max_sweeps, double tol) {
+                     double* __restrict__ Us, double* __restrict__ Vs, int* status, int max_sweeps, double tol,
+                     int dense, const double* __restrict__ V0) {
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ double jsm[];
     double* Aloc = jsm;                       // cpb columns x w
@@ -241,8 +243,8 @@ __global__ void __launch_bounds__(JC_THREADS)
     for (int lc = 0; lc < cpb; ++lc) {
         const int c = me * cpb + lc;
         for (int r = tid; r < w; r += JC_THREADS) {
-            Aloc[(size_t)lc * w + r] = (c < w && r <= c) ? R[r + (int64_t)c * ldr] : 0.0;
-            Vloc[(size_t)lc * w + r] = (r == c) ? 1.0 : 0.0;
+            Aloc[(size_t)lc * w + r] = (c < w && (dense || r <= c)) ? R[r + (int64_t)c * ldr] : 0.0;
+            Vloc[(size_t)lc * w + r] = (V0 && c < w) ? V0[r + (size_t)c * w] : ((r == c) ? 1.0 : 0.0);
         }
     }
     auto colA = [&](int c) -> double* {
@@ -397,80 +399,189 @@ __global__ void __launch_bounds__(JC_THREADS)
     }
 }
 
-// Largest cluster (16, else 8) of k_jacobi_cluster the current device can
-// schedule with the biggest shared-memory request; 0 when neither fits.
+// ---------------------------------------------------------------------------
+// FP32 preconditioner: the same one-sided Jacobi in FP32 on one block (A and
+// V in shared memory, one warp per pair, w <= 128), on R scaled by a power of
+// two so that its largest entry is below 2.  Its V (orthogonal to about
+// 1e-6) is written out as FP64; the caller re-orthogonalises it in FP64 and
+// runs the FP64 Jacobi on R Q0 with V starting at Q0, which then needs a few
+// sweeps instead of the eight to ten from scratch.  FP32 arithmetic runs at
+// 64 times the FP64 rate on GB300, so these sweeps cost little.
+constexpr int J32_THREADS = 1024;
+__global__ void __launch_bounds__(J32_THREADS) k_jacobi32(const double* __restrict__ R, int64_t ldr, int w, int n2,
+                                                         double* __restrict__ Q0, int max_sweeps, float tol) {
+    extern __shared__ float j32[];
+    float* A = j32;               // column c at c * w
+    float* V = j32 + (size_t)w * w;
+    __shared__ int s_rot, s_emax;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int NW = J32_THREADS / 32;
+    if (tid == 0) s_emax = 0;
+    __syncthreads();
+    int em = 0;
+    for (int e = tid; e < w * w; e += J32_THREADS) {
+        const int r = e % w, c = e / w;
+        if (r <= c)
+            em = max(em, (int)(((unsigned long long)__double_as_longlong(R[r + (int64_t)c * ldr]) >> 52) & 0x7FF));
+    }
+    atomicMax(&s_emax, em);
+    __syncthreads();
+    // 2^(1023 - emax) as a double (exact; the largest entry lands in [1, 2))
+    const int ex = 2046 - min(max(s_emax, 1), 2045);
+    const double scale = __longlong_as_double((long long)ex << 52);
+    for (int e = tid; e < w * w; e += J32_THREADS) {
+        const int r = e % w, c = e / w;
+        A[e] = (r <= c) ? (float)(R[r + (int64_t)c * ldr] * scale) : 0.0f;
+        V[e] = (r == c) ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int round = 0; round < n2 - 1; ++round) {
+            for (int k = warp; k < n2 / 2; k += NW) {
+                int p = circle_elem(k, round, n2);
+                int q = circle_elem(n2 - 1 - k, round, n2);
+                if (p > q) { int t = p; p = q; q = t; }
+                if (q >= w) continue;
+                float* ap = A + (size_t)p * w;
+                float* aq = A + (size_t)q * w;
+                float al = 0.f, be = 0.f, ga = 0.f;
+                for (int r = lane; r < w; r += 32) {
+                    const float x = ap[r], y = aq[r];
+                    al = fmaf(x, x, al);
+                    be = fmaf(y, y, be);
+                    ga = fmaf(x, y, ga);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                }
+                if (!(fabsf(ga) > tol * sqrtf(al * be))) continue;  // also skips NaN
+                const float zeta = (be - al) / (2.0f * ga);
+                const float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+                const float cs = rsqrtf(fmaf(t, t, 1.0f));
+                const float sn = cs * t;
+                float* vp = V + (size_t)p * w;
+                float* vq = V + (size_t)q * w;
+                for (int r = lane; r < w; r += 32) {
+                    const float x = ap[r], y = aq[r];
+                    ap[r] = cs * x - sn * y;
+                    aq[r] = sn * x + cs * y;
+                    const float u = vp[r], z = vq[r];
+                    vp[r] = cs * u - sn * z;
+                    vq[r] = sn * u + cs * z;
+                }
+                if (lane == 0) s_rot = 1;
+            }
+            __syncthreads();
+        }
+        const int any = s_rot;
+        __syncthreads();
+        if (!any) break;
+    }
+    for (int e = tid; e < w * w; e += J32_THREADS) Q0[e] = (double)V[e];
+}
+
+__global__ void k_triu(const double* __restrict__ R, int64_t ldr, int w, double* __restrict__ U) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < w * w; e += gridDim.x * blockDim.x) {
+        const int r = e % w, c = e / w;
+        U[e] = (r <= c) ? R[r + (int64_t)c * ldr] : 0.0;
+    }
+}
+
+// Cluster size of k_jacobi_cluster per device: 16 until a launch of that
+// size is refused, then 8, then 0 (the cooperative grid kernel).
+std::mutex g_jc_mu;
+std::unordered_map<int, int> g_jc_size;
+
 int jacobi_cluster_blocks() {
-    static std::mutex mu;
-    static std::unordered_map<int, int> cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(dev);
-    if (it != cache.end()) return it->second;
-    int best = 0;
+    std::lock_guard<std::mutex> lk(g_jc_mu);
+    auto it = g_jc_size.find(dev);
+    if (it != g_jc_size.end()) return it->second;
     if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
         cudaGetLastError();
-    for (int g : {16, 8}) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)g);
-        cfg.blockDim = dim3(JC_THREADS);
-        cfg.dynamicSmemBytes = 48 * 1024;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = (unsigned)g;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, k_jacobi_cluster, &cfg) == cudaSuccess && n > 0) {
-            best = g;
-            break;
-        }
-        cudaGetLastError();
-    }
-    cache[dev] = best;
-    return best;
+    g_jc_size[dev] = 16;
+    return 16;
+}
+
+void jacobi_cluster_refused(int g) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_jc_mu);
+    g_jc_size[dev] = (g > 8) ? 8 : 0;
 }
 
 }  // namespace
 
 size_t jacobi_scratch_elems(int w) { return (size_t)2 * w * w; }
 
+cudaError_t jacobi32_precondition(const double* R, int64_t ldr, int w, double* Q0, int max_sweeps, cudaStream_t st) {
+    if (w <= 0) return cudaSuccess;
+    if (w > 128) return cudaErrorInvalidValue;
+    const size_t shm = sizeof(float) * (size_t)2 * w * w;
+    static thread_local size_t configured = 0;
+    if (shm > 48 * 1024 && shm > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (e != cudaSuccess) return e;
+        configured = shm;
+    }
+    const int n2 = w + (w & 1);
+    k_jacobi32<<<1, J32_THREADS, shm, st>>>(R, ldr, w, n2, Q0, max_sweeps, (float)w * 5.9604645e-8f);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t triu_copy(const double* R, int64_t ldr, int w, double* U, cudaStream_t st) {
+    if (w <= 0) return cudaSuccess;
+    k_triu<<<(unsigned)std::min(cdiv((int64_t)w * w, 256), (int64_t)1024), 256, 0, st>>>(R, ldr, w, U);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
 cudaError_t jacobi_svd(const double* R, int64_t ldr, int w, double* D, double* Us, double* Vs, double* scratch,
                        unsigned* bar, int* counters, int* status, int max_sweeps, cudaStream_t st,
-                       bool allow_cluster) {
+                       bool allow_cluster, bool dense, const double* V0) {
+    const int dn = dense ? 1 : 0;
     if (w <= 0) return cudaSuccess;
     int n2 = w + (w & 1);
     double tol = (double)w * 1.1102230246251565e-16;
-    // cluster variant when A and V fit in the cluster's shared memory
-    const int gcl = jacobi_cluster_blocks();
-    if (allow_cluster && gcl > 0) {
+    // cluster variant when A and V fit in the cluster's shared memory; a
+    // cluster size the device refuses at launch is not tried again
+    for (int gcl = jacobi_cluster_blocks(); allow_cluster && gcl > 0; gcl = jacobi_cluster_blocks()) {
         const int cpb = (n2 + gcl - 1) / gcl;
         const size_t shm_cluster = sizeof(double) * ((size_t)2 * cpb * w + cpb);
-        if (shm_cluster <= 200 * 1024) {
-            static thread_local size_t configured = 0;
-            if (shm_cluster > 48 * 1024 && shm_cluster > configured) {
-                cudaError_t e = cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)shm_cluster);
-                if (e != cudaSuccess) return e;
-                configured = shm_cluster;
-            }
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)gcl);
-            cfg.blockDim = dim3(JC_THREADS);
-            cfg.dynamicSmemBytes = shm_cluster;
-            cfg.stream = st;
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = (unsigned)gcl;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            trace_count(1);
-            return cudaLaunchKernelEx(&cfg, k_jacobi_cluster, R, ldr, w, n2, cpb, D, Us, Vs, status, max_sweeps, tol);
+        if (shm_cluster > 200 * 1024) break;
+        static thread_local size_t configured = 0;
+        if (shm_cluster > 48 * 1024 && shm_cluster > configured) {
+            cudaError_t e = cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)shm_cluster);
+            if (e != cudaSuccess) return e;
+            configured = shm_cluster;
         }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)gcl);
+        cfg.blockDim = dim3(JC_THREADS);
+        cfg.dynamicSmemBytes = shm_cluster;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)gcl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaError_t e =
+            cudaLaunchKernelEx(&cfg, k_jacobi_cluster, R, ldr, w, n2, cpb, D, Us, Vs, status, max_sweeps, tol, dn, V0);
+        if (e == cudaSuccess) {
+            trace_count(1);
+            return cudaSuccess;
+        }
+        cudaGetLastError();  // a refused configuration leaves no sticky error
+        jacobi_cluster_refused(gcl);
     }
     int G = std::max(1, n2 / 2);
     double* A = scratch;
@@ -478,9 +589,10 @@ cudaError_t jacobi_svd(const double* R, int64_t ldr, int w, double* D, double* U
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     size_t shm = sizeof(double) * (size_t)w;
-    void* args[] = {(void*)&R, (void*)&ldr, (void*)&w, (void*)&n2, (void*)&A, (void*)&V, (void*)&D,
-                    (void*)&Us, (void*)&Vs, (void*)&bar, (void*)&counters, (void*)&status,
-                    (void*)&max_sweeps, (void*)&tol};
+    void* args[] = {(void*)&R,      (void*)&ldr,        (void*)&w,   (void*)&n2,  (void*)&A,
+                    (void*)&V,      (void*)&D,          (void*)&Us,  (void*)&Vs,  (void*)&bar,
+                    (void*)&counters, (void*)&status,   (void*)&max_sweeps, (void*)&tol, (void*)&dn,
+                    (void*)&V0};
     trace_count(1);
     if (w <= 128)
         return cudaLaunchCooperativeKernel((const void*)k_jacobi<128>, dim3(G), dim3(128), args, shm, st);
