@@ -41,6 +41,8 @@ DTYPES = {"fp64": "f64", "bf16": "f64+bf16-sketch", "fp16": "f64+fp16-sketch",
           "emul_bf16": "f64 (products emulated on bf16 tensor cores)+bf16-sketch"}
 
 
+E2E_STEPS = 2   # timed end-to-end calls after one untimed call
+
 def measured_peak(key: str, fallback: float) -> float:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -404,18 +406,25 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
         torch.cuda.empty_cache()
         if dist:
             dist.barrier()
-        t0 = time.perf_counter()
+        # one untimed call (the library's device buffers are allocated once and
+        # cached), then E2E_STEPS timed calls, each with both copies inside
         st = rutv.randutv_factor_host(m, n, Ah, m, b, q, 0, Uh, Th, Vh, prec)
-        t_e2e = time.perf_counter() - t0
         if st != rutv.RANDUTV_OK:
             raise rutv.RandUTVError(st, "randutv_factor_host")
+        t0 = time.perf_counter()
+        for _ in range(E2E_STEPS):
+            st = rutv.randutv_factor_host(m, n, Ah, m, b, q, 0, Uh, Th, Vh, prec)
+            if st != rutv.RANDUTV_OK:
+                raise rutv.RandUTVError(st, "randutv_factor_host")
+        t_e2e = (time.perf_counter() - t0) / E2E_STEPS
         if dist:
             t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             t_e2e = float(t.item())
         e2e = {"value": world * F / t_e2e / 1e12, "unit": "TFLOP/s", "s_per_factorization": t_e2e,
                "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * (m * n + m * m + n * n),
-               "api": "randutv_factor_host (pinned host buffers, copies and device allocation inside)"}
+               "steps": E2E_STEPS, "warmup": 1,
+               "api": "randutv_factor_host (pinned host buffers; H2D of A and D2H of U, T, V inside every timed call)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

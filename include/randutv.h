@@ -18,7 +18,9 @@
  *  - m >= n >= 0 is required (T upper triangular, Sec. 3.1); b >= 1; q >= 0.
  *  - U == NULL or V == NULL selects the "no orthonormal matrices" mode of
  *    Sec. 6 (T only, or T plus one factor); the work for the missing factor
- *    is skipped.
+ *    is skipped.  U and V are accumulated after the last block step from the
+ *    reflectors each step keeps (backward order, as LAPACK's dorgqr), which
+ *    gives the same factors as updating them at every step, up to rounding.
  *  - T may alias A when lda == m.
  *  - The Gaussian matrix of block step i is G(r, c) = Box-Muller of
  *    Philox4x64-10(counter = (r/4, c, i, 0), key = (seed, 0)), so results are
@@ -56,7 +58,7 @@ typedef enum {
     RANDUTV_SKETCH_FP16_SCALED = 2, /* as BF16 with FP16 operands and a per-step scale */
     RANDUTV_SKETCH_FP32 = 3,        /* sketch in FP32 (CUDA cores); used by the batched path */
     RANDUTV_FP64_EMULATED = 4,      /* every FP64 product emulated on BF16 tensor cores (Ozaki scheme,
-                                       7 x 7-bit digits, exact FP32 chunks, double-float accumulation);
+                                       8 digits of 7 bits, exact FP32 chunks, double-float accumulation);
                                        panels, T factors and the small SVD stay FP64 */
     RANDUTV_EMULATED_SKETCH_BF16 = 5 /* RANDUTV_FP64_EMULATED with the BF16 sketch of RANDUTV_SKETCH_BF16 */
 } randutv_precision;
@@ -106,9 +108,12 @@ size_t randutv_workspace_size(int64_t m, int64_t n, int b, int prec);
 
 /*
  * randutv_factor_host -- randutv_factor on HOST buffers: copies A to the device,
- * factors it, copies U, T, V back (U or V NULL skips that factor).  Allocates
- * and frees its own device buffers.  A (lda >= m), U (m x m), T (m x n),
- * V (n x n) are host pointers, column-major.  Synchronous.
+ * factors it, copies U, T, V back (U or V NULL skips that factor).  A (lda >= m),
+ * U (m x m), T (m x n), V (n x n) are host pointers, column-major; page-locked
+ * (pinned) host memory gives full copy bandwidth.  The device copies of A/T, U
+ * and V live in buffers the library caches per device and grows as needed
+ * (like the workspace), so repeated calls do not allocate; calls on one device
+ * must therefore not overlap (from several host threads).  Synchronous.
  */
 randutv_status randutv_factor_host(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q,
                                    uint64_t seed, double* U, double* T, double* V, int prec);

@@ -32,35 +32,62 @@ namespace {
 constexpr int PNT = 256;          // threads per block of the panel kernel
 constexpr int kMaxChunk = 4096;   // rows per block (shared-memory bound)
 
+// Cross-block sums.  GB300 retires one FP64 warp instruction per 64 clocks
+// per sub-partition, so one lane summing all G partials of a column in a
+// dependent chain would take G x 64 clocks.  Instead tpc lanes (a power of
+// two, as many as the 256 threads allow for the columns left) each sum the
+// g = lane (mod tpc) terms, and a shuffle tree combines them: a fixed order,
+// so every block gets the same bits.
+__device__ __forceinline__ double split_colsum(const double* __restrict__ pp, int G, int w, int c, bool active,
+                                               int sub, int tpc) {
+    double s0 = 0.0, s1 = 0.0;
+    if (active) {
+        int g = sub;
+        for (; g + tpc < G; g += 2 * tpc) {
+            s0 += __ldcg(pp + (size_t)g * w + c);
+            s1 += __ldcg(pp + (size_t)(g + tpc) * w + c);
+        }
+        if (g < G) s0 += __ldcg(pp + (size_t)g * w + c);
+    }
+    double s = s0 + s1;
+    for (int o = tpc / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 // SLAB = true keeps the block's rows [r0, r0 + chunk) of the panel in shared
-// memory for the whole factorization (one load, one store); false works on
-// the panel in global memory (for slabs that do not fit).
+// memory for the whole factorization (one load, one store), column c at
+// c * ldp with ldp = 1 (mod 16) so that lanes walking along a row hit
+// distinct banks; false works on the panel in global memory.
 template <bool SLAB>
 __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_t ld, int len, int w,
-                                                  double* __restrict__ tau, double* __restrict__ part,
+                                                  double* __restrict__ tau, double* __restrict__ part_d,
                                                   double* __restrict__ piv, unsigned* bar, int* status,
-                                                  int chunk) {
+                                                  int chunk, int ldp) {
     extern __shared__ double smem[];
+    constexpr int NW = PNT / 32;
     double* xsb0 = smem;
     double* xsb1 = smem + chunk;
     double* sred = smem + 2 * chunk;
     double* wv = sred + w;
-    double* slab = wv + w;  // chunk x w, column-major (SLAB only)
-    __shared__ double s_scalars[4];
+    double* wred = wv + w;        // NW x w: per-warp partial dot products
+    double* slab = wred + NW * w; // ldp x w (SLAB only)
+    double* part = part_d;        // [parity][block][column]
+    __shared__ double s_scalars[5];
 
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int NW = PNT / 32;
     const int r0 = cta * chunk;
     const int r1 = min(len, r0 + chunk);
     const int nr = max(0, r1 - r0);
+    const int RB = (nr + NW - 1) / NW;  // rows per warp in the column-parallel passes
+    const int t0 = min(nr, warp * RB), t1 = min(nr, t0 + RB);
     unsigned target = 0;
     // entry (r0 + t, c) of the panel, t < nr: own rows only
     auto PX = [&](int t, int c) -> double& {
-        return SLAB ? slab[t + (size_t)c * chunk] : P[(r0 + t) + (int64_t)c * ld];
+        return SLAB ? slab[t + (size_t)c * ldp] : P[(r0 + t) + (int64_t)c * ld];
     };
     if (SLAB) {
         for (int c = warp; c < w; c += NW)
-            for (int t = lane; t < nr; t += 32) slab[t + (size_t)c * chunk] = P[(r0 + t) + (int64_t)c * ld];
+            for (int t = lane; t < nr; t += 32) slab[t + (size_t)c * ldp] = P[(r0 + t) + (int64_t)c * ld];
         __syncthreads();
     }
 
@@ -70,14 +97,19 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
         xsb0[t] = (r > 0) ? PX(t, 0) : 0.0;
     }
     __syncthreads();
-    for (int c = warp; c < w; c += NW) {
-        double acc = 0.0;
-        for (int t = lane; t < nr; t += 32) {
-            double y = (c == 0) ? xsb0[t] : PX(t, c);
-            acc += xsb0[t] * y;
+    for (int c0 = 0; c0 < w; c0 += 32) {  // lanes over columns, warps over rows
+        const int c = c0 + lane;
+        if (c < w) {
+            double acc = 0.0;
+            for (int t = t0; t < t1; ++t) acc = fma(xsb0[t], c == 0 ? xsb0[t] : PX(t, c), acc);
+            wred[warp * w + c] = acc;
         }
-        acc = warp_sum(acc);
-        if (lane == 0) part[(size_t)cta * w + c] = acc;
+    }
+    __syncthreads();
+    for (int c = tid; c < w; c += PNT) {
+        double acc = wred[c];
+        for (int k = 1; k < NW; ++k) acc += wred[k * w + c];
+        part[(size_t)cta * w + c] = acc;
     }
     if (r0 <= 0 && 0 < r1)
         for (int c = tid; c < w; c += PNT) piv[c] = PX(0, c);
@@ -90,39 +122,47 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
         const double* pp = part + (size_t)p * G * w;
         const double* pv = piv + (size_t)p * w;
 
-        // reduce the partials of columns j..w-1 (fixed block order)
-        for (int c = j + tid; c < w; c += PNT) {
-            double s = 0.0;
-            for (int g = 0; g < G; ++g) s += __ldcg(pp + (size_t)g * w + c);
-            sred[c] = s;
+        // reduce the partials of columns j..w-1, tpc lanes per column
+        {
+            int tpc = 1;
+            while (tpc < 32 && tpc * 2 * (w - j) <= PNT) tpc *= 2;
+            const int cpp = PNT / tpc;  // columns per pass
+            for (int c0 = j; c0 < w; c0 += cpp) {
+                const int c = c0 + tid / tpc;
+                const double v = split_colsum(pp, G, w, c, c < w, tid & (tpc - 1), tpc);
+                if (c < w && (tid & (tpc - 1)) == 0) sred[c] = v;
+            }
         }
+        __syncthreads();
         if (tid == 0) {
             double alpha = __ldcg(pv + j);
             double xi2 = sred[j];
-            double tj = 0.0, beta = alpha, d = 1.0, act = 0.0;
+            double tj = 0.0, beta = alpha, d = 1.0, act = 0.0, rd = 1.0;
             if (!isfinite(xi2) || !isfinite(alpha)) {
                 atomicOr(status, ST_NONFINITE);
             } else if (xi2 > 0.0) {
-                double h = hypot(alpha, sqrt(xi2));
+                const double h = (fabs(alpha) < 1e150 && xi2 < 1e300) ? sqrt(fma(alpha, alpha, xi2))
+                                                                        : hypot(alpha, sqrt(xi2));
                 beta = (alpha >= 0.0) ? -h : h;
                 tj = (beta - alpha) / beta;
                 d = alpha - beta;
+                rd = 1.0 / d;
                 act = 1.0;
             }
             s_scalars[0] = tj;
             s_scalars[1] = beta;
             s_scalars[2] = d;
             s_scalars[3] = act;
+            s_scalars[4] = rd;
             if (cta == 0) tau[j] = tj;
         }
         __syncthreads();
-        const double tj = s_scalars[0], beta = s_scalars[1], d = s_scalars[2];
+        const double tj = s_scalars[0], beta = s_scalars[1], rd = s_scalars[4];
         const bool act = s_scalars[3] != 0.0;
-        for (int c = j + 1 + tid; c < w; c += PNT) wv[c] = act ? (__ldcg(pv + c) + sred[c] / d) : 0.0;
+        for (int c = j + 1 + tid; c < w; c += PNT) wv[c] = act ? fma(sred[c], rd, __ldcg(pv + c)) : 0.0;
 
         // (a) v_r = x_r / d on own rows r > j; P(j,j) = beta; xc keeps tau_j v_r
         if (act) {
-            const double rd = 1.0 / d;
             for (int t = tid; t < nr; t += PNT) {
                 int r = r0 + t;
                 if (r > j) {
@@ -154,31 +194,38 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
             for (int c = j + 1 + tid; c < w; c += PNT) PX(j - r0, c) = __ldcg(pv + c) - tj * wv[c];
         __syncthreads();
 
-        // (b2) columns c >= j+2: apply H_j, accumulate the next column's partials
-        double* pn = part + (size_t)(p ^ 1) * G * w + (size_t)cta * w;
-        for (int c = j + 1 + warp; c < w; c += NW) {
-            double acc = 0.0;
-            if (c == j + 1) {
-                for (int t = lane; t < nr; t += 32) acc += xn[t] * xn[t];
-            } else {
-                const double wc = wv[c];
-                for (int t = lane; t < nr; t += 32) {
-                    int r = r0 + t;
-                    if (r > j) {
-                        double* e = &PX(t, c);
-                        double val = *e;
-                        if (act) {
-                            val = fma(-xc[t], wc, val);
-                            *e = val;
+        // (b2) columns c >= j+2: apply H_j on rows t0..t1 of this warp (lanes
+        // over columns) and accumulate the next column's partials
+        for (int c0 = j + 1; c0 < w; c0 += 32) {
+            const int c = c0 + lane;
+            if (c < w) {
+                double acc = 0.0;
+                if (c == j + 1) {
+                    for (int t = t0; t < t1; ++t) acc = fma(xn[t], xn[t], acc);
+                } else {
+                    const double wc = wv[c];
+                    for (int t = t0; t < t1; ++t) {
+                        if (r0 + t > j) {
+                            double* e = &PX(t, c);
+                            double val = *e;
+                            if (act) {
+                                val = fma(-xc[t], wc, val);
+                                *e = val;
+                            }
+                            acc = fma(xn[t], val, acc);
                         }
-                        acc = fma(xn[t], val, acc);
                     }
                 }
+                wred[warp * w + c] = acc;
             }
-            acc = warp_sum(acc);
-            if (lane == 0) pn[c] = acc;
         }
         __syncthreads();
+        double* pn = part + (size_t)(p ^ 1) * G * w + (size_t)cta * w;
+        for (int c = j + 1 + tid; c < w; c += PNT) {
+            double acc = wred[c];
+            for (int k = 1; k < NW; ++k) acc += wred[k * w + c];
+            pn[c] = acc;
+        }
         if (r0 <= j + 1 && j + 1 < r1)
             for (int c = j + 1 + tid; c < w; c += PNT)
                 piv[(size_t)(p ^ 1) * w + c] = PX(j + 1 - r0, c);
@@ -187,9 +234,10 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
     if (SLAB) {
         __syncthreads();
         for (int c = warp; c < w; c += NW)
-            for (int t = lane; t < nr; t += 32) P[(r0 + t) + (int64_t)c * ld] = slab[t + (size_t)c * chunk];
+            for (int t = lane; t < nr; t += 32) P[(r0 + t) + (int64_t)c * ld] = slab[t + (size_t)c * ldp];
     }
 }
+
 
 __global__ void k_extract_w(const double* __restrict__ P, int64_t ld, int len, int w, double* __restrict__ W) {
     int64_t total = (int64_t)len * w;
@@ -293,8 +341,9 @@ cudaError_t panel_qr(double* P, int64_t ld, int64_t len, int w, double* tau, dou
     if (chunk > kMaxChunk || G > sms) return cudaErrorInvalidValue;
     double* part = scratch;
     double* piv = scratch + (size_t)2 * G * w;
-    const size_t base = sizeof(double) * ((size_t)2 * chunk + (size_t)2 * w);
-    const size_t with_slab = base + sizeof(double) * (size_t)chunk * w;
+    const int ldp = chunk + ((17 - chunk % 16) % 16);  // = 1 (mod 16)
+    const size_t base = sizeof(double) * ((size_t)2 * chunk + (size_t)2 * w + (size_t)(PNT / 32) * w);
+    const size_t with_slab = base + sizeof(double) * (size_t)ldp * w;
     const bool use_slab = with_slab <= 220 * 1024;
     const size_t shm = use_slab ? with_slab : base;
     const void* fn = use_slab ? (const void*)k_panel_qr<true> : (const void*)k_panel_qr<false>;
@@ -307,7 +356,8 @@ cudaError_t panel_qr(double* P, int64_t ld, int64_t len, int w, double* tau, dou
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     int len_i = (int)len;
-    void* args[] = {&P, &ld, &len_i, &w, &tau, &part, &piv, &bar, &status, &chunk};
+    int ldp_i = ldp;
+    void* args[] = {&P, &ld, &len_i, &w, &tau, &part, &piv, &bar, &status, &chunk, &ldp_i};
     trace_count(1);
     return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(PNT), args, shm, st);
 }

@@ -58,9 +58,11 @@ struct Workspace {
     void* oz_rows;    // digit planes of T(:, k0:n) split by rows (kept for one step)
     void* oz_cols;    // digit planes of T22 split by columns (kept for one step)
     double* svdp;     // FP32-preconditioned SVD: Q, Q', Gram, triu(R), R Q (w x w each), or null
+    double* defer;    // reflectors and small factors kept for the deferred U / V accumulation
+    size_t defer_elems;
 };
 
-constexpr int kSlots = 32;
+constexpr int kSlots = 33;
 struct Layout {
     size_t off[kSlots];
     size_t total;
@@ -71,6 +73,18 @@ int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 // widths whose b x b SVD takes the FP32-preconditioned route
 bool svd_precond_width(int w) { return w >= 64 && w <= 128; }
+
+// Doubles kept for the deferred accumulation of U and V: per block step the
+// reflectors W_V ((n - k0) x b) and W_U ((m - k0) x w), T_V, T_U, V_s, U_s
+// (w x w each).
+size_t defer_elems(int64_t m, int64_t n, int b) {
+    size_t e = 0;
+    for (int64_t k0 = 0; k0 < n; k0 += b) {
+        const int64_t w = std::min<int64_t>(b, n - k0);
+        e += (size_t)(n - k0) * b + (size_t)(m - k0) * w + 4 * (size_t)b * b;
+    }
+    return e;
+}
 
 bool lowp_prec(int prec) {
     return prec == RANDUTV_SKETCH_BF16 || prec == RANDUTV_SKETCH_FP16_SCALED || prec == RANDUTV_EMULATED_SKETCH_BF16;
@@ -130,7 +144,8 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec) {
         emulated_prec(prec) ? oz_work_bytes(mx, std::max<int64_t>(wmax, 128), mx) : 0,   // Ozaki digits
         emulated_prec(prec) ? oz_operand_bytes(m, n) : 0,                               // T(:, k0:n) by rows
         emulated_prec(prec) ? oz_operand_bytes(n, m) : 0,                               // T22 by columns
-        svd_precond_width((int)wmax) ? sizeof(double) * 5 * (size_t)wmax * wmax : 0};  // preconditioned SVD
+        svd_precond_width((int)wmax) ? sizeof(double) * 5 * (size_t)wmax * wmax : 0,   // preconditioned SVD
+        sizeof(double) * defer_elems(m, n, b)};                                         // deferred U / V
     size_t o = 0;
     for (int i = 0; i < kSlots; ++i) {
         L.off[i] = o;
@@ -179,7 +194,9 @@ Workspace carve(void* base, const Layout& L) {
     w.oz_bytes = L.off[29] - L.off[28];
     w.oz_rows = L.off[30] > L.off[29] ? (void*)(p + L.off[29]) : nullptr;
     w.oz_cols = L.off[31] > L.off[30] ? (void*)(p + L.off[30]) : nullptr;
-    w.svdp = L.total > L.off[31] ? (double*)(p + L.off[31]) : nullptr;
+    w.svdp = L.off[32] > L.off[31] ? (double*)(p + L.off[31]) : nullptr;
+    w.defer = (double*)(p + L.off[32]);
+    w.defer_elems = (L.total - L.off[32]) / sizeof(double);
     return w;
 }
 
@@ -194,6 +211,32 @@ std::unordered_map<int, CachedWs> g_ws;
 cudaError_t cached_workspace(int dev, size_t bytes, void** out) {
     std::lock_guard<std::mutex> lk(g_ws_mu);
     CachedWs& c = g_ws[dev];
+    if (c.bytes < bytes) {
+        if (c.ptr) {
+            cudaDeviceSynchronize();
+            cudaFree(c.ptr);
+            c.ptr = nullptr;
+            c.bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&c.ptr, bytes);
+        if (e != cudaSuccess) {
+            c.ptr = nullptr;
+            return e;
+        }
+        c.bytes = bytes;
+    }
+    *out = c.ptr;
+    return cudaSuccess;
+}
+
+// Grow-only device buffers for the host-buffer entry point (A/T, U, V),
+// cached per device like the workspace.
+std::mutex g_buf_mu;
+std::unordered_map<int, CachedWs> g_buf[3];
+
+cudaError_t cached_buffer(int dev, int slot, size_t bytes, void** out) {
+    std::lock_guard<std::mutex> lk(g_buf_mu);
+    CachedWs& c = g_buf[slot][dev];
     if (c.bytes < bytes) {
         if (c.ptr) {
             cudaDeviceSynchronize();
@@ -245,6 +288,15 @@ struct Ctx {
     OzCache oc;
     int sms;
     cudaStream_t st;
+    // deferred U / V: what each block step left in w.defer
+    struct Step {
+        int64_t k0;
+        int w;
+        bool sketch;
+        size_t wv, tv, wu, tu, us, vs;  // offsets into w.defer (wv, tv unused without a sketch)
+    };
+    std::vector<Step> steps;
+    size_t defer_top = 0;
 };
 
 cudaError_t gemm(Ctx& c, const char* role, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
@@ -312,6 +364,15 @@ cudaError_t sketch_gemm(Ctx& c, bool tr, int64_t k0, const double* B, int64_t ld
     return oz_cached_product(c, "gemm_sketch", *a, tr ? 0 : k0, M, c.b, B, ldb, Y, ldy);
 }
 
+// Copies a rows x cols matrix (ld lds) into the deferred store; returns its offset.
+cudaError_t defer_put(Ctx& c, const double* src, int64_t lds, int64_t rows, int64_t cols, size_t* off) {
+    *off = c.defer_top;
+    const size_t need = (size_t)rows * cols;
+    if (c.defer_top + need > c.w.defer_elems) return cudaErrorInvalidValue;
+    c.defer_top += need;
+    return copy_matrix(src, lds, c.w.defer + *off, rows, rows, cols, c.st);
+}
+
 // Householder QR of a len x w panel plus its W (explicit) and Tf.
 cudaError_t factor_panel(Ctx& c, double* P, int64_t ld, int64_t len, int w) {
     {
@@ -377,7 +438,10 @@ cudaError_t svd_block(Ctx& c, const double* R, int64_t ldr, int w) {
     double* G = Q1 + w2;
     double* Ru = G + w2;
     double* X = Ru + w2;
-    CK(jacobi32_precondition(R, ldr, w, Q, 12, c.st));
+    {
+        TraceScope t32("jacobi_fp32", 0.0, 0.0, c.st);
+        CK(jacobi32_precondition(R, ldr, w, Q, 8, c.st));
+    }
     for (int it = 0; it < 2; ++it) {
         CK(gemm(c, "svd_precond", true, false, w, w, w, 1.0, Q, w, Q, w, 0.0, G, w));
         CK(copy_matrix(Q, w, Q1, w, w, w, c.st));
@@ -386,6 +450,7 @@ cudaError_t svd_block(Ctx& c, const double* R, int64_t ldr, int w) {
     }
     CK(triu_copy(R, ldr, w, Ru, c.st));
     CK(gemm(c, "svd_precond", false, false, w, w, w, 1.0, Ru, w, Q, w, 0.0, X, w));
+    TraceScope t64("jacobi_fp64", 0.0, 0.0, c.st);
     return jacobi_svd(X, w, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status, kMaxSweeps,
                       c.st, true, true, Q);
 }
@@ -398,7 +463,13 @@ cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
     double* P = T + k0 + k0 * ldt;
     CK(factor_panel(c, P, ldt, mp, w));
     CK(apply_left_t(c, T + k0 + (k0 + w) * ldt, ldt, mp, n - k0 - w, w));
-    if (c.U) CK(apply_right(c, c.U + k0 * m, m, m, mp, w));
+    if (c.steps.empty() || c.steps.back().k0 != k0) c.steps.push_back(Ctx::Step{k0, w, false, 0, 0, 0, 0, 0, 0});
+    Ctx::Step& rec = c.steps.back();
+    rec.w = w;
+    if (c.U) {  // U is accumulated backwards at the end from W_U, T_U, U_s
+        CK(defer_put(c, c.w.W, mp, mp, w, &rec.wu));
+        CK(defer_put(c, c.w.Tf, w, w, w, &rec.tu));
+    }
     CK(svd_block(c, P, ldt, w));
     if (k0 > 0) {  // T(0:k0, blk) := T(0:k0, blk) Vs
         CK(gemm(c, "gemm_svdapply", false, false, k0, w, w, 1.0, T + k0 * ldt, ldt, c.w.Vs, w, 0.0, c.w.tmp, k0));
@@ -410,13 +481,39 @@ cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
         CK(copy_matrix(c.w.tmp, w, T + k0 + (k0 + w) * ldt, ldt, w, nr, c.st));
     }
     CK(set_diag_block(T, ldt, k0, m, w, c.w.D, c.st));
-    if (c.V) {
-        CK(gemm(c, "gemm_svdapply", false, false, n, w, w, 1.0, c.V + k0 * n, n, c.w.Vs, w, 0.0, c.w.tmp, n));
-        CK(copy_matrix(c.w.tmp, n, c.V + k0 * n, n, n, w, c.st));
-    }
-    if (c.U) {
-        CK(gemm(c, "gemm_svdapply", false, false, m, w, w, 1.0, c.U + k0 * m, m, c.w.Us, w, 0.0, c.w.tmp, m));
-        CK(copy_matrix(c.w.tmp, m, c.U + k0 * m, m, m, w, c.st));
+    if (c.V) CK(defer_put(c, c.w.Vs, w, w, w, &rec.vs));
+    if (c.U) CK(defer_put(c, c.w.Us, w, w, w, &rec.us));
+    return cudaSuccess;
+}
+
+// X (len x cols, ld ldx) := (I - W Tf W^T) X with W (len x w, ld len) and
+// the upper triangular Tf (w x w) of a compact WY product Q = I - W Tf W^T.
+cudaError_t apply_left(Ctx& c, const double* W, const double* Tf, double* X, int64_t ldx, int64_t len, int64_t cols,
+                       int w) {
+    if (len <= 0 || cols <= 0) return cudaSuccess;
+    CK(gemm(c, "gemm_accumulate", true, false, w, cols, len, 1.0, W, len, X, ldx, 0.0, c.w.X, w));
+    CK(gemm(c, "gemm_accumulate_tf", false, false, w, cols, w, 1.0, Tf, w, c.w.X, w, 0.0, c.w.X2, w));
+    return gemm(c, "gemm_accumulate", false, false, len, cols, w, -1.0, W, len, c.w.X2, w, 1.0, X, ldx);
+}
+
+// Deferred accumulation of the orthogonal factors (the backward order of
+// LAPACK's dorgqr).  With Q_i = I - W_i Tf_i W_i^T acting on indices >= k0_i
+// and S_i = diag(I, s_i, I) the small-SVD factor at block i,
+//   V = Q_0 S_0 Q_1 S_1 ... ,  so  X := I;  for i = last..0: X := Q_i (S_i X).
+// Before step i, X differs from I only in rows and columns >= k0_i + w_i, so
+// S_i X just writes s_i into the diagonal block and Q_i touches X(k0_i:, k0_i:)
+// only: (n - k0_i)^2 instead of n (n - k0_i) per step, a third less work than
+// updating V at every step.
+cudaError_t accumulate(Ctx& c, double* X, int64_t nx, bool is_v) {
+    CK(set_identity(X, nx, nx, c.st));
+    for (int64_t i = (int64_t)c.steps.size() - 1; i >= 0; --i) {
+        const Ctx::Step& r = c.steps[(size_t)i];
+        double* Xb = X + r.k0 + r.k0 * nx;
+        CK(copy_matrix(c.w.defer + (is_v ? r.vs : r.us), r.w, Xb, nx, r.w, r.w, c.st));
+        if (is_v && !r.sketch) continue;
+        const int w = is_v ? c.b : r.w;
+        CK(apply_left(c, c.w.defer + (is_v ? r.wv : r.wu), c.w.defer + (is_v ? r.tv : r.tu), Xb, nx, nx - r.k0,
+                      nx - r.k0, w));
     }
     return cudaSuccess;
 }
@@ -613,16 +710,21 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
     }
     CK(factor_panel(c, c.w.Y, np, np, b));
     CK(apply_right_T(c, k0, b));
-    if (c.V) CK(apply_right(c, c.V + k0 * n, n, n, np, b));
+    Ctx::Step rec{k0, b, true, 0, 0, 0, 0, 0, 0};
+    if (c.V) {  // V is accumulated backwards at the end from W_V, T_V, V_s
+        CK(defer_put(c, c.w.W, np, np, b, &rec.wv));
+        CK(defer_put(c, c.w.Tf, b, b, b, &rec.tv));
+    }
+    c.steps.push_back(rec);
     return panel_and_svd(c, k0, b);
 }
 
 cudaError_t run_factor(Ctx& c, const double* A, int64_t lda, int64_t stop_after) {
     const int64_t m = c.m, n = c.n;
     if (A != c.T) CK(copy_matrix(A, lda, c.T, c.ldt, m, n, c.st));
-    if (c.U) CK(set_identity(c.U, m, m, c.st));
-    if (c.V) CK(set_identity(c.V, n, n, c.st));
     CK(check_finite(c.T, c.ldt, m, n, c.w.status, c.st));
+    c.steps.clear();
+    c.defer_top = 0;
     for (int64_t i = 0;; ++i) {
         if (stop_after >= 0 && i >= stop_after) break;
         int64_t k0 = i * (int64_t)c.b;
@@ -634,6 +736,8 @@ cudaError_t run_factor(Ctx& c, const double* A, int64_t lda, int64_t stop_after)
         }
         CK(sketch_step(c, i));
     }
+    if (c.V) CK(accumulate(c, c.V, n, true));
+    if (c.U) CK(accumulate(c, c.U, m, false));
     return cudaSuccess;
 }
 
@@ -890,30 +994,26 @@ randutv_status randutv_factor(int64_t m, int64_t n, const double* A, int64_t lda
 randutv_status randutv_factor_host(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q,
                                    uint64_t seed, double* U, double* T, double* V, int prec) {
     if (!args_ok(m, n, A, lda, b, q, T)) return RANDUTV_EINVAL;
-    double *dA = nullptr, *dU = nullptr, *dV = nullptr;
-    size_t bytesT = sizeof(double) * (size_t)m * n;
-    randutv_status rs = RANDUTV_OK;
-    if (cudaMalloc(&dA, std::max<size_t>(bytesT, 8)) != cudaSuccess) return RANDUTV_ENOMEM;
-    if (U && cudaMalloc(&dU, std::max<size_t>(sizeof(double) * (size_t)m * m, 8)) != cudaSuccess) rs = RANDUTV_ENOMEM;
-    if (rs == RANDUTV_OK && V && cudaMalloc(&dV, std::max<size_t>(sizeof(double) * (size_t)n * n, 8)) != cudaSuccess)
-        rs = RANDUTV_ENOMEM;
-    if (rs == RANDUTV_OK && bytesT > 0 &&
-        cudaMemcpy2D(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
-                     cudaMemcpyHostToDevice) != cudaSuccess)
-        rs = RANDUTV_ECUDA;
-    if (rs == RANDUTV_OK)
-        rs = randutv_factor_ex(m, n, dA, m, b, q, seed, U ? dU : nullptr, dA, V ? dV : nullptr, prec, nullptr,
-                               nullptr, 0, -1, nullptr);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RANDUTV_ECUDA;
+    const size_t bytesT = sizeof(double) * (size_t)m * n;
+    const size_t bytesU = sizeof(double) * (size_t)m * m, bytesV = sizeof(double) * (size_t)n * n;
+    void *dA = nullptr, *dU = nullptr, *dV = nullptr;
+    if (cached_buffer(dev, 0, std::max<size_t>(bytesT, 8), &dA) != cudaSuccess) return RANDUTV_ENOMEM;
+    if (U && cached_buffer(dev, 1, std::max<size_t>(bytesU, 8), &dU) != cudaSuccess) return RANDUTV_ENOMEM;
+    if (V && cached_buffer(dev, 2, std::max<size_t>(bytesV, 8), &dV) != cudaSuccess) return RANDUTV_ENOMEM;
+    cudaStream_t st = nullptr;  // legacy default stream
+    if (bytesT > 0 && cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+                                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return RANDUTV_ECUDA;
+    randutv_status rs = randutv_factor_ex(m, n, (double*)dA, m, b, q, seed, (double*)dU, (double*)dA, (double*)dV,
+                                          prec, st, nullptr, 0, -1, nullptr);
     if ((rs == RANDUTV_OK || rs == RANDUTV_ENOCONV) && bytesT > 0) {
-        if (cudaMemcpy(T, dA, bytesT, cudaMemcpyDeviceToHost) != cudaSuccess) rs = RANDUTV_ECUDA;
-        if (U && cudaMemcpy(U, dU, sizeof(double) * (size_t)m * m, cudaMemcpyDeviceToHost) != cudaSuccess)
-            rs = RANDUTV_ECUDA;
-        if (V && cudaMemcpy(V, dV, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost) != cudaSuccess)
-            rs = RANDUTV_ECUDA;
+        if (cudaMemcpyAsync(T, dA, bytesT, cudaMemcpyDeviceToHost, st) != cudaSuccess) return RANDUTV_ECUDA;
+        if (U && cudaMemcpyAsync(U, dU, bytesU, cudaMemcpyDeviceToHost, st) != cudaSuccess) return RANDUTV_ECUDA;
+        if (V && cudaMemcpyAsync(V, dV, bytesV, cudaMemcpyDeviceToHost, st) != cudaSuccess) return RANDUTV_ECUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return RANDUTV_ECUDA;
     }
-    cudaFree(dA);
-    if (dU) cudaFree(dU);
-    if (dV) cudaFree(dV);
     return rs;
 }
 

@@ -300,11 +300,19 @@ __global__ void __launch_bounds__(JC_THREADS)
                 else rot = fabs(ga) > tol * sqrt(al) * sqrt(be);
                 if (!rot) continue;
                 const double d = be - al, g = 2.0 * ga;
-                const double ad = fabs(d), ag = fabs(g);
+                // t from its FP32 value when d and g are within FP32's range
+                // (decided on the exponent bits: no FP64 compares): the FP32
+                // square root and division are cheap, and c = 1/sqrt(1+t^2),
+                // s = c t in FP64 keep the rotation orthogonal to FP64
+                // rounding; an angle off by ~1e-7 only leaves ~1e-7 of the
+                // pair's coupling to a later sweep.
+                const int ed = (int)(((unsigned long long)__double_as_longlong(d) >> 52) & 0x7FF);
+                const int eg = (int)(((unsigned long long)__double_as_longlong(g) >> 52) & 0x7FF);
                 double t;
-                if (ad < 1e150 && ag < 1e150 && ag > 1e-150) {
-                    const double sg = (d == 0.0 || ((d > 0.0) == (g > 0.0))) ? 1.0 : -1.0;
-                    t = sg * ag / (ad + sqrt(fma(d, d, g * g)));
+                if (eg > 1023 - 60 && eg < 1023 + 60 && (ed == 0 || (ed > 1023 - 60 && ed < 1023 + 60))) {
+                    const float df = (float)d, gf = (float)g;
+                    const float sg = (df == 0.0f || ((df > 0.0f) == (gf > 0.0f))) ? 1.0f : -1.0f;
+                    t = (double)(sg * fabsf(gf) / (fabsf(df) + sqrtf(fmaf(df, df, gf * gf))));
                 } else {
                     const double zeta = d / g;
                     t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -439,33 +447,43 @@ __global__ void __launch_bounds__(J32_THREADS) k_jacobi32(const double* __restri
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int round = 0; round < n2 - 1; ++round) {
-            for (int k = warp; k < n2 / 2; k += NW) {
-                int p = circle_elem(k, round, n2);
-                int q = circle_elem(n2 - 1 - k, round, n2);
-                if (p > q) { int t = p; p = q; q = t; }
-                if (q >= w) continue;
+            // sixteen lanes per pair: the two halves of a warp take two pairs
+            for (int k0 = warp * 2; k0 < n2 / 2; k0 += 2 * NW) {
+                const int k = k0 + (lane >> 4), hl = lane & 15;
+                int p = 0, q = 0;
+                bool act = k < n2 / 2;
+                if (act) {
+                    p = circle_elem(k, round, n2);
+                    q = circle_elem(n2 - 1 - k, round, n2);
+                    if (p > q) { int t = p; p = q; q = t; }
+                    act = q < w;
+                }
                 float* ap = A + (size_t)p * w;
                 float* aq = A + (size_t)q * w;
                 float al = 0.f, be = 0.f, ga = 0.f;
-                for (int r = lane; r < w; r += 32) {
-                    const float x = ap[r], y = aq[r];
-                    al = fmaf(x, x, al);
-                    be = fmaf(y, y, be);
-                    ga = fmaf(x, y, ga);
-                }
-                for (int o = 16; o > 0; o >>= 1) {
+                if (act)
+                    for (int r = hl; r < w; r += 16) {
+                        const float x = ap[r], y = aq[r];
+                        al = fmaf(x, x, al);
+                        be = fmaf(y, y, be);
+                        ga = fmaf(x, y, ga);
+                    }
+                for (int o = 8; o > 0; o >>= 1) {
                     al += __shfl_xor_sync(0xffffffffu, al, o);
                     be += __shfl_xor_sync(0xffffffffu, be, o);
                     ga += __shfl_xor_sync(0xffffffffu, ga, o);
                 }
-                if (!(fabsf(ga) > tol * sqrtf(al * be))) continue;  // also skips NaN
-                const float zeta = (be - al) / (2.0f * ga);
-                const float t = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+                if (!act || !(fabsf(ga) > tol * sqrtf(al * be))) continue;  // also skips NaN
+                // fast intrinsics: this sweep only preconditions the FP64 one
+                const float d = be - al, g = 2.0f * ga;
+                const float hyp = __fsqrt_rn(fmaf(d, d, g * g));
+                const float sg = (d == 0.0f || ((d > 0.0f) == (g > 0.0f))) ? 1.0f : -1.0f;
+                const float t = sg * __fdividef(fabsf(g), fabsf(d) + hyp);
                 const float cs = rsqrtf(fmaf(t, t, 1.0f));
                 const float sn = cs * t;
                 float* vp = V + (size_t)p * w;
                 float* vq = V + (size_t)q * w;
-                for (int r = lane; r < w; r += 32) {
+                for (int r = hl; r < w; r += 16) {
                     const float x = ap[r], y = aq[r];
                     ap[r] = cs * x - sn * y;
                     aq[r] = sn * x + cs * y;
@@ -473,7 +491,7 @@ __global__ void __launch_bounds__(J32_THREADS) k_jacobi32(const double* __restri
                     vp[r] = cs * u - sn * z;
                     vq[r] = sn * u + cs * z;
                 }
-                if (lane == 0) s_rot = 1;
+                if (hl == 0) s_rot = 1;
             }
             __syncthreads();
         }
