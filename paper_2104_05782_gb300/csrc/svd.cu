@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(NT) k_jacobi(const double* __restrict__ R, int
 // sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) for zeta = d / g.
 constexpr int JC_THREADS = 128;
 constexpr int JC_LPP = 32;  // lanes per pair
+constexpr int JC_ROWS = 8;  // rows per lane: the cluster variant takes w <= 256
 
 __global__ void __launch_bounds__(JC_THREADS)
     k_jacobi_cluster(const double* __restrict__ R, int64_t ldr, int w, int n2, int cpb, double* __restrict__ D,
@@ -271,16 +272,29 @@ __global__ void __launch_bounds__(JC_THREADS)
                     if (p > q) { int t = p; p = q; q = t; }
                     act = q < w;
                 }
+                // both columns of A and V in registers (rows sub, sub + 32, ...),
+                // all loads issued before the reductions
                 double* ap = act ? colA(p) : nullptr;
                 double* aq = act ? colA(q) : nullptr;
+                double* vp = act ? colV(p) : nullptr;
+                double* vq = act ? colV(q) : nullptr;
+                double xr[JC_ROWS], yr[JC_ROWS], ur[JC_ROWS], zr[JC_ROWS];
+#pragma unroll
+                for (int i = 0; i < JC_ROWS; ++i) {
+                    const int r = sub + JC_LPP * i;
+                    const bool ok = act && r < w;
+                    xr[i] = ok ? ap[r] : 0.0;
+                    yr[i] = ok ? aq[r] : 0.0;
+                    ur[i] = ok ? vp[r] : 0.0;
+                    zr[i] = ok ? vq[r] : 0.0;
+                }
                 double al = 0.0, be = 0.0, ga = 0.0;
-                if (act)
-                    for (int r = sub; r < w; r += JC_LPP) {
-                        const double x = ap[r], y = aq[r];
-                        al = fma(x, x, al);
-                        be = fma(y, y, be);
-                        ga = fma(x, y, ga);
-                    }
+#pragma unroll
+                for (int i = 0; i < JC_ROWS; ++i) {
+                    al = fma(xr[i], xr[i], al);
+                    be = fma(yr[i], yr[i], be);
+                    ga = fma(xr[i], yr[i], ga);
+                }
 #pragma unroll
                 for (int o = JC_LPP / 2; o > 0; o >>= 1) {
                     al += __shfl_xor_sync(0xffffffffu, al, o);
@@ -288,15 +302,18 @@ __global__ void __launch_bounds__(JC_THREADS)
                     ga += __shfl_xor_sync(0xffffffffu, ga, o);
                 }
                 if (!act) continue;
-                if (!isfinite(al) || !isfinite(be) || !isfinite(ga)) {
+                // exponent fields: non-finite checks and range tests without FP64 compares
+                const int eal = (int)(((unsigned long long)__double_as_longlong(al) >> 52) & 0x7FF);
+                const int ebe = (int)(((unsigned long long)__double_as_longlong(be) >> 52) & 0x7FF);
+                const int ega = (int)(((unsigned long long)__double_as_longlong(ga) >> 52) & 0x7FF);
+                if (eal == 0x7FF || ebe == 0x7FF || ega == 0x7FF) {
                     if (sub == 0) atomicOr(status, ST_NONFINITE);
                     continue;
                 }
                 // |gamma| > tol sqrt(alpha beta), squared where that cannot under- or overflow
-                const double pr = al * be;
                 bool rot;
-                if (ga == 0.0) rot = false;
-                else if (pr > 1e-290 && pr < 1e290) rot = ga * ga > tol2 * pr;
+                if (ega == 0) rot = false;
+                else if (eal + ebe > 2046 - 960 && eal + ebe < 2046 + 960) rot = ga * ga > tol2 * (al * be);
                 else rot = fabs(ga) > tol * sqrt(al) * sqrt(be);
                 if (!rot) continue;
                 const double d = be - al, g = 2.0 * ga;
@@ -319,15 +336,15 @@ __global__ void __launch_bounds__(JC_THREADS)
                 }
                 const double cs = rsqrt(fma(t, t, 1.0));
                 const double sn = cs * t;
-                double* vp = colV(p);
-                double* vq = colV(q);
-                for (int r = sub; r < w; r += JC_LPP) {
-                    const double x = ap[r], y = aq[r];
-                    ap[r] = cs * x - sn * y;
-                    aq[r] = sn * x + cs * y;
-                    const double u = vp[r], z = vq[r];
-                    vp[r] = cs * u - sn * z;
-                    vq[r] = sn * u + cs * z;
+#pragma unroll
+                for (int i = 0; i < JC_ROWS; ++i) {
+                    const int r = sub + JC_LPP * i;
+                    if (r < w) {
+                        ap[r] = fma(-sn, yr[i], cs * xr[i]);
+                        aq[r] = fma(sn, xr[i], cs * yr[i]);
+                        vp[r] = fma(-sn, zr[i], cs * ur[i]);
+                        vq[r] = fma(sn, ur[i], cs * zr[i]);
+                    }
                 }
                 if (sub == 0) s_flag = 1;
             }
@@ -447,33 +464,40 @@ __global__ void __launch_bounds__(J32_THREADS) k_jacobi32(const double* __restri
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int round = 0; round < n2 - 1; ++round) {
-            // sixteen lanes per pair: the two halves of a warp take two pairs
-            for (int k0 = warp * 2; k0 < n2 / 2; k0 += 2 * NW) {
-                const int k = k0 + (lane >> 4), hl = lane & 15;
-                int p = 0, q = 0;
-                bool act = k < n2 / 2;
-                if (act) {
-                    p = circle_elem(k, round, n2);
-                    q = circle_elem(n2 - 1 - k, round, n2);
-                    if (p > q) { int t = p; p = q; q = t; }
-                    act = q < w;
-                }
+            // one warp per pair (rows lane, lane + 32, ...: conflict-free
+            // shared-memory rows), both columns of A and V in registers
+            for (int k = warp; k < n2 / 2; k += NW) {
+                int p = circle_elem(k, round, n2);
+                int q = circle_elem(n2 - 1 - k, round, n2);
+                if (p > q) { int t = p; p = q; q = t; }
+                if (q >= w) continue;
                 float* ap = A + (size_t)p * w;
                 float* aq = A + (size_t)q * w;
+                float* vp = V + (size_t)p * w;
+                float* vq = V + (size_t)q * w;
+                float xr[4], yr[4], ur[4], zr[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = lane + 32 * i;
+                    const bool ok = r < w;
+                    xr[i] = ok ? ap[r] : 0.f;
+                    yr[i] = ok ? aq[r] : 0.f;
+                    ur[i] = ok ? vp[r] : 0.f;
+                    zr[i] = ok ? vq[r] : 0.f;
+                }
                 float al = 0.f, be = 0.f, ga = 0.f;
-                if (act)
-                    for (int r = hl; r < w; r += 16) {
-                        const float x = ap[r], y = aq[r];
-                        al = fmaf(x, x, al);
-                        be = fmaf(y, y, be);
-                        ga = fmaf(x, y, ga);
-                    }
-                for (int o = 8; o > 0; o >>= 1) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    al = fmaf(xr[i], xr[i], al);
+                    be = fmaf(yr[i], yr[i], be);
+                    ga = fmaf(xr[i], yr[i], ga);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
                     al += __shfl_xor_sync(0xffffffffu, al, o);
                     be += __shfl_xor_sync(0xffffffffu, be, o);
                     ga += __shfl_xor_sync(0xffffffffu, ga, o);
                 }
-                if (!act || !(fabsf(ga) > tol * sqrtf(al * be))) continue;  // also skips NaN
+                if (!(fabsf(ga) > tol * sqrtf(al * be))) continue;  // also skips NaN
                 // fast intrinsics: this sweep only preconditions the FP64 one
                 const float d = be - al, g = 2.0f * ga;
                 const float hyp = __fsqrt_rn(fmaf(d, d, g * g));
@@ -481,17 +505,17 @@ __global__ void __launch_bounds__(J32_THREADS) k_jacobi32(const double* __restri
                 const float t = sg * __fdividef(fabsf(g), fabsf(d) + hyp);
                 const float cs = rsqrtf(fmaf(t, t, 1.0f));
                 const float sn = cs * t;
-                float* vp = V + (size_t)p * w;
-                float* vq = V + (size_t)q * w;
-                for (int r = hl; r < w; r += 16) {
-                    const float x = ap[r], y = aq[r];
-                    ap[r] = cs * x - sn * y;
-                    aq[r] = sn * x + cs * y;
-                    const float u = vp[r], z = vq[r];
-                    vp[r] = cs * u - sn * z;
-                    vq[r] = sn * u + cs * z;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = lane + 32 * i;
+                    if (r < w) {
+                        ap[r] = cs * xr[i] - sn * yr[i];
+                        aq[r] = sn * xr[i] + cs * yr[i];
+                        vp[r] = cs * ur[i] - sn * zr[i];
+                        vq[r] = sn * ur[i] + cs * zr[i];
+                    }
                 }
-                if (hl == 0) s_rot = 1;
+                if (lane == 0) s_rot = 1;
             }
             __syncthreads();
         }
@@ -572,7 +596,7 @@ cudaError_t jacobi_svd(const double* R, int64_t ldr, int w, double* D, double* U
     for (int gcl = jacobi_cluster_blocks(); allow_cluster && gcl > 0; gcl = jacobi_cluster_blocks()) {
         const int cpb = (n2 + gcl - 1) / gcl;
         const size_t shm_cluster = sizeof(double) * ((size_t)2 * cpb * w + cpb);
-        if (shm_cluster > 200 * 1024) break;
+        if (shm_cluster > 200 * 1024 || w > JC_LPP * JC_ROWS) break;
         static thread_local size_t configured = 0;
         if (shm_cluster > 48 * 1024 && shm_cluster > configured) {
             cudaError_t e = cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
