@@ -221,7 +221,7 @@ __global__ void k_oz_split(const double* __restrict__ X, int64_t ld, int R, int 
 // 256-column accumulator buffers alternate per 128-deep chunk: the drain of
 // one chunk overlaps the MMAs of the next.
 constexpr int OZ_TN = 32;                               // output columns per job
-constexpr int OZ_AST = 8;                               // A ring stages
+constexpr int OZ_AST = 10;                              // A ring stages
 constexpr int OZ_BST = 2;                               // B ring stages
 constexpr int OZ_EPI = 8;                               // drain / epilogue warps
 constexpr int OZ_THREADS = (OZ_EPI + 2) * 32;
@@ -396,6 +396,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
         for (int j = blockIdx.x; j < jb.njobs; j += gridDim.x) {
             int m0, n0, z, kb0, nkb;
             jb.get(j, m0, n0, z, kb0, nkb);
+            // this job's C tile, row exponent and column exponents are loaded
+            // before the accumulators are waited for, so their latency hides
+            // behind the MMAs (the tile is read and written by this job only)
+            const int r = m0 + quad * 32 + lane;
+            const int cb = n0 + half * 16;
+            const int ncols = (r < M) ? min(16, N - cb) : 0;
+            const int er = (ncols > 0) ? eA[r] : INT_MIN;
+            int ec[16];
+            double cv[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                ec[c] = (c < ncols) ? eB[cb + c] : INT_MIN;
+                cv[c] = (!partial && bmode != 0 && c < ncols) ? C[r + (int64_t)(cb + c) * ldc] : 0.0;
+            }
             float hi[16], lo[16];
 #pragma unroll
             for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0.0f;
@@ -451,19 +465,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                 s_abort = 1;
                 break;
             }
-            const int r = m0 + quad * 32 + lane;
-            const int cb = n0 + half * 16;
-            const int ncols = min(16, N - cb);
-            if (r < M && ncols > 0) {
-                const int er = eA[r];
-                int ec[16];
-                double cv[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c) ec[c] = (c < ncols) ? eB[cb + c] : INT_MIN;
-                if (!partial && bmode != 0) {  // all loads of C in flight at once
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) cv[c] = (c < ncols) ? C[r + (int64_t)(cb + c) * ldc] : 0.0;
-                }
+            if (ncols > 0) {
                 // amode: 1 alpha = +1, 2 alpha = -1 (folded into the sign), 0 general
                 const long long sgn = (amode == 2) ? (long long)(1ull << 63) : 0ll;
                 double* Pz = partial ? P + (size_t)z * (size_t)M * (size_t)N : nullptr;
