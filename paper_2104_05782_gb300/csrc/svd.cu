@@ -311,10 +311,16 @@ __global__ void __launch_bounds__(JC_THREADS)
                     continue;
                 }
                 // |gamma| > tol sqrt(alpha beta), squared where that cannot under- or overflow
-                bool rot;
-                if (ega == 0) rot = false;
-                else if (eal + ebe > 2046 - 960 && eal + ebe < 2046 + 960) rot = ga * ga > tol2 * (al * be);
-                else rot = fabs(ga) > tol * sqrt(al) * sqrt(be);
+                bool rot, big = true;
+                if (ega == 0) {
+                    rot = false;
+                } else if (eal + ebe > 2046 - 960 && eal + ebe < 2046 + 960) {
+                    const double g2 = ga * ga, pr = al * be;
+                    rot = g2 > tol2 * pr;
+                    big = g2 > 1e-16 * pr;  // coupling above 1e-8
+                } else {
+                    rot = fabs(ga) > tol * sqrt(al) * sqrt(be);
+                }
                 if (!rot) continue;
                 const double d = be - al, g = 2.0 * ga;
                 // t from its FP32 value when d and g are within FP32's range
@@ -336,6 +342,10 @@ __global__ void __launch_bounds__(JC_THREADS)
                 }
                 const double cs = rsqrt(fma(t, t, 1.0));
                 const double sn = cs * t;
+                // a rotation by more than ~1e-7 rad (nearly equal columns
+                // rotate by up to 45 degrees however small their coupling)
+                // can re-couple earlier pairs: not a final sweep
+                big = big || (int)(((unsigned long long)__double_as_longlong(t) >> 52) & 0x7FF) > 1023 - 24;
 #pragma unroll
                 for (int i = 0; i < JC_ROWS; ++i) {
                     const int r = sub + JC_LPP * i;
@@ -346,13 +356,19 @@ __global__ void __launch_bounds__(JC_THREADS)
                         vq[r] = fma(sn, ur[i], cs * zr[i]);
                     }
                 }
-                if (sub == 0) s_flag = 1;
+                if (sub == 0) atomicOr((int*)&s_flag, big ? 3 : 1);
             }
             cluster.sync();
         }
+        // converged after a sweep without rotations, or after one whose
+        // couplings were all below 1e-8 and whose rotation angles were all
+        // below ~1e-7: each later rotation then disturbs an earlier pair by
+        // at most its angle times that pair's coupling (~1e-15), and the
+        // FP32-derived angles leave at most ~1e-7 of a coupling behind, all
+        // below the tolerance, so the next sweep would rotate nothing
         int any = 0;
         for (int b = 0; b < G; ++b) any |= *cluster.map_shared_rank(&s_flag, b);
-        converged = (any == 0);
+        converged = (any & 2) == 0;
         cluster.sync();  // every block has read the flags before they are reset
     }
     if (!converged && me == 0 && tid == 0) atomicOr(status, ST_NOCONV);
