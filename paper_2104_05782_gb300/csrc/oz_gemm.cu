@@ -207,9 +207,11 @@ __global__ void k_oz_split(const double* __restrict__ X, int64_t ld, int R, int 
 
 // ---------------------------------------------------------------- product
 // Persistent kernel, one CTA per SM.  A job is one 128 x 32 output tile over
-// one K range (a split-K slice); jobs are dealt round-robin and consecutive
-// job ids are neighbouring column tiles, so CTAs running together share the
-// A digit tiles in L2.
+// one K range (a split-K slice).  CTAs take jobs from a global counter in
+// order, so neighbouring column tiles run together and share the A digit
+// tiles in L2, and a CTA that starts late (its SM busy with a concurrent
+// kernel) simply takes fewer jobs.  The producer warp takes each job and
+// passes its index to the MMA and drain warps through a 4-slot ring.
 //   warp 8    : TMA producer (ring of OZ_AST A digit tiles, ring of OZ_BST
 //               stacked B digit sets)
 //   warp 9    : MMA issuer
@@ -229,7 +231,9 @@ constexpr int OZ_A_BYTES = OZ_TM * OZ_TK * 2;           // 16 KB
 constexpr int OZ_BPLANE = OZ_TN * OZ_TK * 2;            // 4 KB
 constexpr int OZ_B_BYTES = OZ_S * OZ_BPLANE;            // 32 KB
 constexpr int OZ_ACC = OZ_S * OZ_TN;                    // 256 TMEM columns per buffer
-constexpr int OZ_SMEM = OZ_AST * OZ_A_BYTES + OZ_BST * OZ_B_BYTES + 1024 + 256;
+// dynamic shared memory: the rings plus slack for the 1024-byte alignment
+// (the barriers live in static shared memory)
+constexpr int OZ_SMEM = OZ_AST * OZ_A_BYTES + OZ_BST * OZ_B_BYTES + 1024;
 
 // FP32 value x times 2^sh, built as an FP64 bit pattern with integer
 // instructions (exact); zero and FP32 subnormals give 0; returns false when
@@ -263,20 +267,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                                                             double alpha, double beta, double* __restrict__ C,
                                                             int64_t ldc, OzJobs jb, double* __restrict__ P,
                                                             int* status, int a_plane, int a_row0, int b_plane,
-                                                            int b_row0, int amode, int bmode) {
+                                                            int b_row0, int amode, int bmode, int* jobctr) {
     extern __shared__ __align__(1024) uint8_t oz_raw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)oz_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* Abuf = sm;                                   // OZ_AST x 16 KB
     uint8_t* Bbuf = sm + OZ_AST * OZ_A_BYTES;             // OZ_BST x 32 KB
-    uint64_t* bars = (uint64_t*)(Bbuf + OZ_BST * OZ_B_BYTES);
+    __shared__ __align__(8) uint64_t bars[2 * OZ_AST + 2 * OZ_BST + 2 + 2 + 4 + 4];
+    __shared__ uint32_t tslot[1];
     uint64_t* a_full = bars;                   // [OZ_AST]
     uint64_t* a_empty = a_full + OZ_AST;       // [OZ_AST]
     uint64_t* b_full = a_empty + OZ_AST;       // [OZ_BST]
     uint64_t* b_empty = b_full + OZ_BST;       // [OZ_BST]
     uint64_t* acc_full = b_empty + OZ_BST;     // [2] chunk accumulated
     uint64_t* acc_empty = acc_full + 2;        // [2] chunk drained
-    uint32_t* tslot = (uint32_t*)(acc_empty + 2);
+    uint64_t* job_full = acc_empty + 2;        // [4] job index published
+    uint64_t* job_empty = job_full + 4;        // [4] job index read by all
     __shared__ volatile int s_abort;
+    __shared__ volatile int s_job[4];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool partial = jb.njobs > jb.tiles_m * jb.tiles_n;  // split-K: FP64 partials to P
@@ -294,6 +301,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
             bar_init(&acc_full[i], 1);
             bar_init(&acc_empty[i], OZ_EPI);
         }
+        for (int i = 0; i < 4; ++i) {
+            bar_init(&job_full[i], 1);
+            bar_init(&job_empty[i], 1 + OZ_EPI);  // the MMA warp and every drain warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -310,7 +321,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
     if (warp == OZ_EPI) {
         if (lane == 0) {  // ---------------- TMA producer
             long long ia = 0, ib = 0;
-            for (int j = blockIdx.x; j < jb.njobs && !s_abort; j += gridDim.x) {
+            for (int n = 0; !s_abort; ++n) {
+                const int slot = n & 3;
+                if (!bar_wait(&job_empty[slot], (uint32_t)(((n >> 2) & 1) ^ 1))) { s_abort = 1; break; }
+                const int j = atomicAdd(jobctr, 1);
+                s_job[slot] = (j < jb.njobs) ? j : -1;
+                bar_arrive(&job_full[slot]);
+                if (j >= jb.njobs) break;
                 int m0, n0, z, kb0, nkb;
                 jb.get(j, m0, n0, z, kb0, nkb);
                 for (int kb = 0; kb < nkb && !s_abort; ++kb) {
@@ -339,7 +356,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
     } else if (warp == OZ_EPI + 1) {
         if (lane == 0) {  // ---------------- MMA issuer
             long long ia = 0, ib = 0, chunk = 0;
-            for (int j = blockIdx.x; j < jb.njobs && !s_abort; j += gridDim.x) {
+            for (int n = 0; !s_abort; ++n) {
+                const int slot = n & 3;
+                if (!bar_wait(&job_full[slot], (uint32_t)((n >> 2) & 1))) { s_abort = 1; break; }
+                const int j = s_job[slot];
+                bar_arrive(&job_empty[slot]);
+                if (j < 0) break;
                 int m0, n0, z, kb0, nkb;
                 jb.get(j, m0, n0, z, kb0, nkb);
                 for (int kb = 0; kb < nkb && !s_abort; ++kb) {
@@ -393,7 +415,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
     } else {  // ---------------- warps 0-7: drain TMEM, epilogue
         const int quad = warp & 3, half = warp >> 2;  // TMEM lanes 32 quad.., columns 16 half..
         long long chunk = 0;
-        for (int j = blockIdx.x; j < jb.njobs; j += gridDim.x) {
+        for (int n = 0;; ++n) {
+            const int slot = n & 3;
+            const bool got = __all_sync(0xffffffffu, bar_wait(&job_full[slot], (uint32_t)((n >> 2) & 1)));
+            if (!got || s_abort) {
+                if (!got && lane == 0) atomicOr(status, ST_TIMEOUT);
+                s_abort = 1;
+                break;
+            }
+            const int j = s_job[slot];
+            __syncwarp();
+            if (lane == 0) bar_arrive(&job_empty[slot]);
+            if (j < 0) break;
             int m0, n0, z, kb0, nkb;
             jb.get(j, m0, n0, z, kb0, nkb);
             // this job's C tile, row exponent and column exponents are loaded
@@ -608,18 +641,22 @@ cudaError_t oz_product(const OzOperand& a, int64_t a_row0, const OzOperand& b, i
     jb.tiles_m = (int)cdiv(M, OZ_TM);
     jb.tiles_n = (int)cdiv(N, OZ_TN);
     jb.nkb_all = (int)cdiv(K, OZ_TK);
-    const int s0 = oz_splits(M, N, K, sms, p_bytes);
+    const int s0 = oz_splits(M, N, K, sms, p_bytes > 256 ? p_bytes - 256 : 0);
     jb.kbs = (int)(cdiv(cdiv(jb.nkb_all, OZ_CHUNK), s0) * OZ_CHUNK);  // whole chunks per split
     const int splits = (int)cdiv(jb.nkb_all, jb.kbs);
     const int64_t njobs = (int64_t)jb.tiles_m * jb.tiles_n * splits;
     if (njobs > INT_MAX) return cudaErrorInvalidValue;
     jb.njobs = (int)njobs;
     const unsigned grid = (unsigned)std::min<int64_t>(njobs, sms);
+    // the job counter sits in the first 256 bytes of P; the partials follow
+    int* jobctr = (int*)P;
+    P = (double*)((char*)P + 256);
+    if (cudaMemsetAsync(jobctr, 0, sizeof(int), st) != cudaSuccess) return cudaErrorInvalidValue;
     const int amode = (alpha == 1.0) ? 1 : (alpha == -1.0 ? 2 : 0);
     const int bmode = (beta == 0.0) ? 0 : (beta == 1.0 ? 1 : 2);
     k_oz_gemm<<<grid, OZ_THREADS, OZ_SMEM, st>>>(ma, mb, (int)M, (int)N, a.e + a_row0, b.e + b_row0, alpha, beta, C,
                                                    ldc, jb, P, status, (int)a.plane, (int)a_row0, (int)b.plane,
-                                                   (int)b_row0, amode, bmode);
+                                                   (int)b_row0, amode, bmode, jobctr);
     trace_count(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || splits == 1) return e;

@@ -261,6 +261,31 @@ cudaError_t cached_buffer(int dev, int slot, size_t bytes, void** out) {
         if (e_ != cudaSuccess) return e_;     \
     } while (0)
 
+// A second stream and two events per device: the FP32 Jacobi of a block step
+// runs on it while the left update of the same step runs on the caller's
+// stream.  Created on first use, kept for the life of the process.
+struct SideStream {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ready = nullptr, done = nullptr;
+};
+std::mutex g_side_mu;
+std::unordered_map<int, SideStream> g_side;
+
+cudaError_t side_stream(SideStream** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    SideStream& s = g_side[dev];
+    if (!s.st) {
+        if ((e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&s.ready, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    *out = &s;
+    return cudaSuccess;
+}
+
 enum SketchMode { MODE_FIXED = 0, MODE_LEARNED = 1, MODE_TRACE = 2 };
 
 // Splits of the trailing matrix reused by the emulated products of one block
@@ -427,21 +452,46 @@ cudaError_t apply_left_t(Ctx& c, double* C, int64_t ldc, int64_t len, int64_t co
 // 1e-6), two Newton-Schulz steps Q := Q (3I - Q^T Q) / 2 make it orthogonal
 // to FP64 rounding, and the FP64 Jacobi then runs on R Q with V starting at
 // Q, so Vs = Q W and R = Us diag(D) Vs^T as before, after a few sweeps.
-cudaError_t svd_block(Ctx& c, const double* R, int64_t ldr, int w) {
+// First half: the FP32 Jacobi (w x w, one block) on a side stream, started
+// right after the panel QR so that it overlaps the left update; R (the
+// upper triangle of the panel's first w columns) is not touched by that
+// update.  Returns whether the preconditioned route was started.
+cudaError_t svd_block_begin(Ctx& c, const double* R, int64_t ldr, int w, bool* started) {
+    *started = false;
+    if (!c.w.svdp || !svd_precond_width(w)) return cudaSuccess;
+    SideStream* ss = nullptr;
+    CK(side_stream(&ss));
+    CK(cudaEventRecord(ss->ready, c.st));
+    CK(cudaStreamWaitEvent(ss->st, ss->ready, 0));
+    {
+        TraceScope t32("jacobi_fp32", 0.0, 0.0, ss->st);
+        CK(jacobi32_precondition(R, ldr, w, c.w.svdp, 8, ss->st));
+    }
+    CK(cudaEventRecord(ss->done, ss->st));
+    *started = true;
+    return cudaSuccess;
+}
+
+// SVD of the w x w upper triangle of R (Sec. 3.2.3).  For 64 <= w <= 128 the
+// FP64 Jacobi is preconditioned: an FP32 Jacobi gives Q (orthogonal to about
+// 1e-6; started by svd_block_begin), two Newton-Schulz steps
+// Q := Q (3I - Q^T Q) / 2 make it orthogonal to FP64 rounding, and the FP64
+// Jacobi then runs on R Q with V starting at Q, so Vs = Q W and
+// R = Us diag(D) Vs^T as before, after a few sweeps.
+cudaError_t svd_block(Ctx& c, const double* R, int64_t ldr, int w, bool started) {
     TraceScope tsv("jacobi_svd", 0.0, 8.0 * 3.0 * (double)w * w, c.st);
-    if (!c.w.svdp || !svd_precond_width(w))
+    if (!started)
         return jacobi_svd(R, ldr, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status,
                           kMaxSweeps, c.st);
+    SideStream* ss = nullptr;
+    CK(side_stream(&ss));
+    CK(cudaStreamWaitEvent(c.st, ss->done, 0));
     const size_t w2 = (size_t)w * w;
     double* Q = c.w.svdp;
     double* Q1 = Q + w2;
     double* G = Q1 + w2;
     double* Ru = G + w2;
     double* X = Ru + w2;
-    {
-        TraceScope t32("jacobi_fp32", 0.0, 0.0, c.st);
-        CK(jacobi32_precondition(R, ldr, w, Q, 8, c.st));
-    }
     for (int it = 0; it < 2; ++it) {
         CK(gemm(c, "svd_precond", true, false, w, w, w, 1.0, Q, w, Q, w, 0.0, G, w));
         CK(copy_matrix(Q, w, Q1, w, w, w, c.st));
@@ -462,6 +512,8 @@ cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
     double* T = c.T;
     double* P = T + k0 + k0 * ldt;
     CK(factor_panel(c, P, ldt, mp, w));
+    bool pre = false;
+    CK(svd_block_begin(c, P, ldt, w, &pre));
     CK(apply_left_t(c, T + k0 + (k0 + w) * ldt, ldt, mp, n - k0 - w, w));
     if (c.steps.empty() || c.steps.back().k0 != k0) c.steps.push_back(Ctx::Step{k0, w, false, 0, 0, 0, 0, 0, 0});
     Ctx::Step& rec = c.steps.back();
@@ -470,7 +522,7 @@ cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
         CK(defer_put(c, c.w.W, mp, mp, w, &rec.wu));
         CK(defer_put(c, c.w.Tf, w, w, w, &rec.tu));
     }
-    CK(svd_block(c, P, ldt, w));
+    CK(svd_block(c, P, ldt, w, pre));
     if (k0 > 0) {  // T(0:k0, blk) := T(0:k0, blk) Vs
         CK(gemm(c, "gemm_svdapply", false, false, k0, w, w, 1.0, T + k0 * ldt, ldt, c.w.Vs, w, 0.0, c.w.tmp, k0));
         CK(copy_matrix(c.w.tmp, k0, T + k0 * ldt, ldt, k0, w, c.st));
@@ -1003,9 +1055,13 @@ randutv_status randutv_factor_host(int64_t m, int64_t n, const double* A, int64_
     if (U && cached_buffer(dev, 1, std::max<size_t>(bytesU, 8), &dU) != cudaSuccess) return RANDUTV_ENOMEM;
     if (V && cached_buffer(dev, 2, std::max<size_t>(bytesV, 8), &dV) != cudaSuccess) return RANDUTV_ENOMEM;
     cudaStream_t st = nullptr;  // legacy default stream
-    if (bytesT > 0 && cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
-                                        cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return RANDUTV_ECUDA;
+    if (bytesT > 0) {  // one contiguous copy when A has no padding, else a pitched copy
+        const cudaError_t e = (lda == m)
+                                  ? cudaMemcpyAsync(dA, A, bytesT, cudaMemcpyHostToDevice, st)
+                                  : cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda,
+                                                      sizeof(double) * m, n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return RANDUTV_ECUDA;
+    }
     randutv_status rs = randutv_factor_ex(m, n, (double*)dA, m, b, q, seed, (double*)dU, (double*)dA, (double*)dV,
                                           prec, st, nullptr, 0, -1, nullptr);
     if ((rs == RANDUTV_OK || rs == RANDUTV_ENOCONV) && bytesT > 0) {

@@ -173,3 +173,21 @@ def test_host_entry_point_matches_device(rutv):
     assert rutv.randutv_factor_host(m, n, Af, m, b, q, 3, U, T, V) == rutv.RANDUTV_OK
     got = gpu_factor(rutv, A, b, q, 3)
     assert np.array_equal(T, got[1]) and np.array_equal(U, got[0]) and np.array_equal(V, got[2])
+
+
+def test_host_entry_point_padded_lda(rutv):
+    """A with a leading dimension larger than m goes through the pitched copy
+    and gives the same bits as the unpadded call."""
+    m, n, b, q, pad = 150, 120, 32, 1, 7
+    A = synthetic.test_matrix(m, n, "geometric10", 18, 19)
+    big = np.full((m + pad, n), np.nan, order="F")
+    big[:m, :] = A
+    outs = []
+    for src, lda in ((np.asfortranarray(A), m), (big, m + pad)):
+        U = np.zeros((m, m), order="F")
+        T = np.zeros((m, n), order="F")
+        V = np.zeros((n, n), order="F")
+        assert rutv.randutv_factor_host(m, n, src, lda, b, q, 4, U, T, V) == rutv.RANDUTV_OK
+        outs.append((U, T, V))
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
