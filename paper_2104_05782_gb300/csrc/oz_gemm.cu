@@ -321,10 +321,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
     if (warp == OZ_EPI) {
         if (lane == 0) {  // ---------------- TMA producer
             long long ia = 0, ib = 0;
-            for (int n = 0; !s_abort; ++n) {
+            int jnext = atomicAdd(jobctr, 1);  // fetched one job ahead: the atomic's latency hides
+            for (int n = 0; !s_abort; ++n) {   // behind the current job's copies
                 const int slot = n & 3;
                 if (!bar_wait(&job_empty[slot], (uint32_t)(((n >> 2) & 1) ^ 1))) { s_abort = 1; break; }
-                const int j = atomicAdd(jobctr, 1);
+                const int j = jnext;
+                if (j < jb.njobs) jnext = atomicAdd(jobctr, 1);
                 s_job[slot] = (j < jb.njobs) ? j : -1;
                 bar_arrive(&job_full[slot]);
                 if (j >= jb.njobs) break;

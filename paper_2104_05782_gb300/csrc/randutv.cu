@@ -60,9 +60,14 @@ struct Workspace {
     double* svdp;     // FP32-preconditioned SVD: Q, Q', Gram, triu(R), R Q (w x w each), or null
     double* defer;    // reflectors and small factors kept for the deferred U / V accumulation
     size_t defer_elems;
+    // the side stream's own scratch (the small SVD and its application run there)
+    void* oz2;
+    size_t oz2_bytes;
+    double* tmp2;
+    double* part2;
 };
 
-constexpr int kSlots = 33;
+constexpr int kSlots = 36;
 struct Layout {
     size_t off[kSlots];
     size_t total;
@@ -145,7 +150,10 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec) {
         emulated_prec(prec) ? oz_operand_bytes(m, n) : 0,                               // T(:, k0:n) by rows
         emulated_prec(prec) ? oz_operand_bytes(n, m) : 0,                               // T22 by columns
         svd_precond_width((int)wmax) ? sizeof(double) * 5 * (size_t)wmax * wmax : 0,   // preconditioned SVD
-        sizeof(double) * defer_elems(m, n, b)};                                         // deferred U / V
+        sizeof(double) * defer_elems(m, n, b),                                          // deferred U / V
+        emulated_prec(prec) ? 2 * oz_operand_bytes(mx, std::max<int64_t>(wmax, 128)) + 8192 : 0,  // side Ozaki
+        sizeof(double) * (size_t)mx * wmax,                                             // side tmp
+        sizeof(double) * part};                                                         // side partials
     size_t o = 0;
     for (int i = 0; i < kSlots; ++i) {
         L.off[i] = o;
@@ -196,7 +204,11 @@ Workspace carve(void* base, const Layout& L) {
     w.oz_cols = L.off[31] > L.off[30] ? (void*)(p + L.off[30]) : nullptr;
     w.svdp = L.off[32] > L.off[31] ? (double*)(p + L.off[31]) : nullptr;
     w.defer = (double*)(p + L.off[32]);
-    w.defer_elems = (L.total - L.off[32]) / sizeof(double);
+    w.defer_elems = (L.off[33] - L.off[32]) / sizeof(double);
+    w.oz2 = (void*)(p + L.off[33]);
+    w.oz2_bytes = L.off[34] - L.off[33];
+    w.tmp2 = (double*)(p + L.off[34]);
+    w.part2 = (double*)(p + L.off[35]);
     return w;
 }
 
@@ -266,7 +278,9 @@ cudaError_t cached_buffer(int dev, int slot, size_t bytes, void** out) {
 // stream.  Created on first use, kept for the life of the process.
 struct SideStream {
     cudaStream_t st = nullptr;
-    cudaEvent_t ready = nullptr, done = nullptr;
+    cudaEvent_t ready = nullptr, done = nullptr;      // FP32 Jacobi overlapping the left update
+    cudaEvent_t panel = nullptr, right = nullptr;     // main -> side: panel factored, right update done
+    cudaEvent_t applied = nullptr;                    // side -> main: small SVD applied to T
 };
 std::mutex g_side_mu;
 std::unordered_map<int, SideStream> g_side;
@@ -281,6 +295,9 @@ cudaError_t side_stream(SideStream** out) {
         if ((e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&s.ready, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&s.panel, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&s.right, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&s.applied, cudaEventDisableTiming)) != cudaSuccess) return e;
     }
     *out = &s;
     return cudaSuccess;
@@ -322,6 +339,10 @@ struct Ctx {
     };
     std::vector<Step> steps;
     size_t defer_top = 0;
+    // overlap of the small SVD with the next block step (fixed-q mode)
+    bool overlap = false;
+    int64_t pending = -1;        // step whose small SVD still has to be applied to T
+    bool applied_pending = false;  // an application was queued that the main stream has not waited for
 };
 
 cudaError_t gemm(Ctx& c, const char* role, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
@@ -390,19 +411,27 @@ cudaError_t sketch_gemm(Ctx& c, bool tr, int64_t k0, const double* B, int64_t ld
 }
 
 // Copies a rows x cols matrix (ld lds) into the deferred store; returns its offset.
-cudaError_t defer_put(Ctx& c, const double* src, int64_t lds, int64_t rows, int64_t cols, size_t* off) {
+cudaError_t defer_put(Ctx& c, const double* src, int64_t lds, int64_t rows, int64_t cols, size_t* off,
+                      cudaStream_t st) {
     *off = c.defer_top;
     const size_t need = (size_t)rows * cols;
     if (c.defer_top + need > c.w.defer_elems) return cudaErrorInvalidValue;
     c.defer_top += need;
-    return copy_matrix(src, lds, c.w.defer + *off, rows, rows, cols, c.st);
+    return copy_matrix(src, lds, c.w.defer + *off, rows, rows, cols, st);
 }
+cudaError_t defer_put(Ctx& c, const double* src, int64_t lds, int64_t rows, int64_t cols, size_t* off) {
+    return defer_put(c, src, lds, rows, cols, off, c.st);
+}
+
+// SMs for the cooperative panel QR: with the small SVD overlapping on the
+// side stream, room is left for its 16-block cluster and the FP32 block.
+int panel_sms(const Ctx& c) { return (c.overlap && c.sms > 64) ? c.sms - 17 : c.sms; }
 
 // Householder QR of a len x w panel plus its W (explicit) and Tf.
 cudaError_t factor_panel(Ctx& c, double* P, int64_t ld, int64_t len, int w) {
     {
         TraceScope ts("panel_qr", 2.0 * (double)len * w * w, 16.0 * (double)len * w, c.st);
-        CK(panel_qr(P, ld, len, w, c.w.tau, c.w.pscr, c.w.bars, c.w.status, c.sms, c.st));
+        CK(panel_qr(P, ld, len, w, c.w.tau, c.w.pscr, c.w.bars, c.w.status, panel_sms(c), c.st));
     }
     {
         TraceScope ts("extract_w", 0.0, 16.0 * (double)len * w, c.st);
@@ -505,6 +534,106 @@ cudaError_t svd_block(Ctx& c, const double* R, int64_t ldr, int w, bool started)
                       c.st, true, true, Q);
 }
 
+// ---- overlap of the small SVD with the next block step (fixed-q mode) ------
+// Step i's b x b SVD needs only its panel QR, and its application to T
+// touches columns blk_i and rows blk_i; step i+1's sketch, panel and left
+// update touch neither.  So the SVD runs on the side stream while the main
+// stream goes on: the side stream waits for the panel, computes the SVD,
+// then waits for step i+1's right update and applies Us, Vs.  The rows
+// blk_i of T(:, J2') that step i+1's right update reads are then not yet
+// multiplied by Us^T; left and right multiplications commute, so applying
+// Us^T after that update gives the same T.  The main stream waits for an
+// application before the next sketch (the row split of T(:, J2') must see
+// it) and before U, V are accumulated.
+
+// A copy of the context that runs on the side stream with its own scratch.
+Ctx side_ctx(const Ctx& c, cudaStream_t st2) {
+    Ctx c2 = c;
+    c2.st = st2;
+    c2.w.oz = c.w.oz2;
+    c2.w.oz_bytes = c.w.oz2_bytes;
+    c2.w.tmp = c.w.tmp2;
+    c2.w.part = c.w.part2;
+    c2.steps.clear();
+    return c2;
+}
+
+// The SVD of R (w x w upper triangle) on the side stream, after the panel.
+cudaError_t svd_side(Ctx& c, const double* R, int64_t ldr, int w) {
+    SideStream* ss = nullptr;
+    CK(side_stream(&ss));
+    CK(cudaEventRecord(ss->panel, c.st));
+    CK(cudaStreamWaitEvent(ss->st, ss->panel, 0));
+    Ctx c2 = side_ctx(c, ss->st);
+    TraceScope tsv("jacobi_svd", 0.0, 8.0 * 3.0 * (double)w * w, c2.st);
+    if (!c.w.svdp || !svd_precond_width(w))
+        return jacobi_svd(R, ldr, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status,
+                          kMaxSweeps, c2.st);
+    const size_t w2 = (size_t)w * w;
+    double* Q = c.w.svdp;
+    double* Q1 = Q + w2;
+    double* G = Q1 + w2;
+    double* Ru = G + w2;
+    double* X = Ru + w2;
+    {
+        TraceScope t32("jacobi_fp32", 0.0, 0.0, c2.st);
+        CK(jacobi32_precondition(R, ldr, w, Q, 8, c2.st));
+    }
+    for (int it = 0; it < 2; ++it) {
+        CK(gemm(c2, "svd_precond", true, false, w, w, w, 1.0, Q, w, Q, w, 0.0, G, w));
+        CK(copy_matrix(Q, w, Q1, w, w, w, c2.st));
+        CK(gemm(c2, "svd_precond", false, false, w, w, w, -0.5, Q, w, G, w, 1.5, Q1, w));
+        std::swap(Q, Q1);
+    }
+    CK(triu_copy(R, ldr, w, Ru, c2.st));
+    CK(gemm(c2, "svd_precond", false, false, w, w, w, 1.0, Ru, w, Q, w, 0.0, X, w));
+    TraceScope t64("jacobi_fp64", 0.0, 0.0, c2.st);
+    return jacobi_svd(X, w, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status, kMaxSweeps,
+                      c2.st, true, true, Q);
+}
+
+// Applies the pending step's Us, Vs on the side stream once the main stream
+// has reached this point (after the next right update), then signals.
+cudaError_t flush_pending(Ctx& c) {
+    if (c.pending < 0) return cudaSuccess;
+    SideStream* ss = nullptr;
+    CK(side_stream(&ss));
+    CK(cudaEventRecord(ss->right, c.st));
+    CK(cudaStreamWaitEvent(ss->st, ss->right, 0));
+    Ctx c2 = side_ctx(c, ss->st);
+    Ctx::Step& rec = c.steps[(size_t)c.pending];
+    const int64_t k0 = rec.k0, m = c.m, n = c.n, ldt = c.ldt;
+    const int w = rec.w;
+    double* T = c.T;
+    if (k0 > 0) {  // T(0:k0, blk) := T(0:k0, blk) Vs
+        CK(gemm(c2, "gemm_svdapply", false, false, k0, w, w, 1.0, T + k0 * ldt, ldt, c.w.Vs, w, 0.0, c2.w.tmp, k0));
+        CK(copy_matrix(c2.w.tmp, k0, T + k0 * ldt, ldt, k0, w, c2.st));
+    }
+    const int64_t nr = n - k0 - w;
+    if (nr > 0) {  // T(blk, k0+w:n) := Us^T T(blk, k0+w:n)
+        CK(gemm(c2, "gemm_svdapply", true, false, w, nr, w, 1.0, c.w.Us, w, T + k0 + (k0 + w) * ldt, ldt, 0.0,
+                c2.w.tmp, w));
+        CK(copy_matrix(c2.w.tmp, w, T + k0 + (k0 + w) * ldt, ldt, w, nr, c2.st));
+    }
+    CK(set_diag_block(T, ldt, k0, m, w, c.w.D, c2.st));
+    if (c.V) CK(defer_put(c, c.w.Vs, w, w, w, &rec.vs, c2.st));
+    if (c.U) CK(defer_put(c, c.w.Us, w, w, w, &rec.us, c2.st));
+    CK(cudaEventRecord(ss->applied, c2.st));
+    c.pending = -1;
+    c.applied_pending = true;
+    return cudaSuccess;
+}
+
+// The main stream waits for the last queued application of a small SVD.
+cudaError_t wait_applied(Ctx& c) {
+    if (!c.applied_pending) return cudaSuccess;
+    SideStream* ss = nullptr;
+    CK(side_stream(&ss));
+    CK(cudaStreamWaitEvent(c.st, ss->applied, 0));
+    c.applied_pending = false;
+    return cudaSuccess;
+}
+
 // Panel QR of T(k0:m, k0:k0+w), left update, small SVD and its application.
 cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
     const int64_t m = c.m, n = c.n, ldt = c.ldt;
@@ -512,12 +641,26 @@ cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
     double* T = c.T;
     double* P = T + k0 + k0 * ldt;
     CK(factor_panel(c, P, ldt, mp, w));
+    if (c.steps.empty() || c.steps.back().k0 != k0) c.steps.push_back(Ctx::Step{k0, w, false, 0, 0, 0, 0, 0, 0});
+    c.steps.back().w = w;
+    if (c.overlap) {
+        // a sketch step flushed its predecessor after its right update; the
+        // final block has none, so the previous step is applied here
+        CK(flush_pending(c));
+        CK(svd_side(c, P, ldt, w));
+        c.pending = (int64_t)c.steps.size() - 1;
+        CK(apply_left_t(c, T + k0 + (k0 + w) * ldt, ldt, mp, n - k0 - w, w));
+        Ctx::Step& rec = c.steps.back();
+        if (c.U) {  // U is accumulated backwards at the end from W_U, T_U, U_s
+            CK(defer_put(c, c.w.W, mp, mp, w, &rec.wu));
+            CK(defer_put(c, c.w.Tf, w, w, w, &rec.tu));
+        }
+        return cudaSuccess;  // applied after the next right update (flush_pending)
+    }
     bool pre = false;
     CK(svd_block_begin(c, P, ldt, w, &pre));
     CK(apply_left_t(c, T + k0 + (k0 + w) * ldt, ldt, mp, n - k0 - w, w));
-    if (c.steps.empty() || c.steps.back().k0 != k0) c.steps.push_back(Ctx::Step{k0, w, false, 0, 0, 0, 0, 0, 0});
     Ctx::Step& rec = c.steps.back();
-    rec.w = w;
     if (c.U) {  // U is accumulated backwards at the end from W_U, T_U, U_s
         CK(defer_put(c, c.w.W, mp, mp, w, &rec.wu));
         CK(defer_put(c, c.w.Tf, w, w, w, &rec.tu));
@@ -658,7 +801,7 @@ cudaError_t fp64_iterate(Ctx& c, int64_t k0, double* Y, int iters) {
 cudaError_t block_features(Ctx& c, int64_t k0, int64_t np) {
     TraceScope ts("learnq_features", 0.0, 16.0 * (double)np * c.b, c.st);
     CK(copy_matrix(c.w.Y, np, c.w.Z, np, np, c.b, c.st));
-    CK(panel_qr(c.w.Z, np, np, c.b, c.w.tau, c.w.pscr, c.w.bars, c.w.status, c.sms, c.st));
+    CK(panel_qr(c.w.Z, np, np, c.b, c.w.tau, c.w.pscr, c.w.bars, c.w.status, panel_sms(c), c.st));
     return learnq_features(c.T, c.ldt, k0, k0 > 0 ? c.b : 0, c.w.Z, np, c.b, c.w.feat, c.st);
 }
 
@@ -700,6 +843,7 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
     const bool lowp = lowp_prec(c.prec) && b % 16 == 0 && b <= 256 && mp >= 128 && np >= 128;
     const LowpShape ls = lowp_shape(c, mp, np);
     int iters = c.q;
+    CK(wait_applied(c));  // the previous application must reach T before its rows are split
     if (c.mode == MODE_FIXED) {
         if (lowp) {
             CK(lowp_begin(c, i, T22, ls));
@@ -762,6 +906,7 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
     }
     CK(factor_panel(c, c.w.Y, np, np, b));
     CK(apply_right_T(c, k0, b));
+    CK(flush_pending(c));  // the previous step's Us^T may now reach rows blk_{i-1}
     Ctx::Step rec{k0, b, true, 0, 0, 0, 0, 0, 0};
     if (c.V) {  // V is accumulated backwards at the end from W_V, T_V, V_s
         CK(defer_put(c, c.w.W, np, np, b, &rec.wv));
@@ -777,6 +922,11 @@ cudaError_t run_factor(Ctx& c, const double* A, int64_t lda, int64_t stop_after)
     CK(check_finite(c.T, c.ldt, m, n, c.w.status, c.st));
     c.steps.clear();
     c.defer_top = 0;
+    c.pending = -1;
+    c.applied_pending = false;
+    // the learned mode reads the previous diagonal block for its features, and
+    // the trace mode uses the SVD buffers itself: both stay serial
+    c.overlap = (c.mode == MODE_FIXED);
     for (int64_t i = 0;; ++i) {
         if (stop_after >= 0 && i >= stop_after) break;
         int64_t k0 = i * (int64_t)c.b;
@@ -788,6 +938,8 @@ cudaError_t run_factor(Ctx& c, const double* A, int64_t lda, int64_t stop_after)
         }
         CK(sketch_step(c, i));
     }
+    CK(flush_pending(c));
+    CK(wait_applied(c));
     if (c.V) CK(accumulate(c, c.V, n, true));
     if (c.U) CK(accumulate(c, c.U, m, false));
     return cudaSuccess;

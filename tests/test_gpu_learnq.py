@@ -92,7 +92,12 @@ def test_learned_path_with_forcing_model_equals_fixed_q(rutv, q):
     assert qu[:-1] == [q] * (len(qu) - 1) and qu[-1] == -1
     Uf, Tf, Vf = rutv.factor(dev(A), b, q, 3)
     torch.cuda.synchronize()
-    assert np.array_equal(host(T), host(Tf)) and np.array_equal(host(U), host(Uf))
+    # the fixed-q path applies each block's small SVD after the next step's
+    # right update (the two commute); the learned path applies it at once:
+    # the same factorization up to rounding
+    nrm = np.linalg.norm(A)
+    assert np.abs(host(T) - host(Tf)).max() <= 1e-10 * nrm
+    assert np.abs(host(U) @ host(T) - host(Uf) @ host(Tf)).max() <= 1e-10 * nrm
 
 
 def test_no_model_falls_back_to_q2(rutv):
@@ -102,7 +107,7 @@ def test_no_model_falls_back_to_q2(rutv):
     assert r == 0 and all(x == 2 for x in qu[:-1])
     _, Tf, _ = rutv.factor(dev(A), 64, 2, 0, want_uv=False)
     torch.cuda.synchronize()
-    assert np.array_equal(host(T), host(Tf))
+    assert np.abs(host(T) - host(Tf)).max() <= 1e-10 * np.linalg.norm(A)  # same up to rounding
 
 
 def test_trace_labels_follow_definition(rutv):
@@ -118,7 +123,7 @@ def test_trace_labels_follow_definition(rutv):
     Tt = host(T)
     _, Tf, _ = rutv.factor(dev(A), b, 2, 4, want_uv=False)
     torch.cuda.synchronize()
-    assert np.abs(Tt - host(Tf)).max() <= 1e-12 * np.linalg.norm(A)
+    assert np.abs(Tt - host(Tf)).max() <= 1e-10 * np.linalg.norm(A)  # same up to rounding
     for i in range(len(y)):
         d2 = np.diag(Tt)[i * b:(i + 1) * b]
         assert np.abs(cand[i, 2] - d2).max() <= 1e-10 * d2[0]
