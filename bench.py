@@ -318,6 +318,7 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
             "fp64_equivalent_tflops": g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None,
             "launches": g_launch, "share_of_traced_time": g_ms / tot_ms if tot_ms else None,
+            "share_of_step_time": g_ms / (args.steps * ms_per_step) if ms_per_step else None,
             "avg_flops_per_launch": bf_fl / max(g_launch, 1), "avg_ms_per_launch": g_ms / max(g_launch, 1),
         }
     else:
@@ -334,6 +335,7 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
                               "scaled by the average flops per launch",
             "peak_source": "cuBLAS DGEMM 8192^3 measured in this run (MEASURED_PEAKS.json has no FP64 entry)",
             "launches": g_launch, "share_of_traced_time": g_ms / tot_ms if tot_ms else None,
+            "share_of_step_time": g_ms / (args.steps * ms_per_step) if ms_per_step else None,
             "avg_flops_per_launch": g_fl / max(g_launch, 1),
             "avg_ms_per_launch": g_ms / max(g_launch, 1),
         }
