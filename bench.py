@@ -156,6 +156,17 @@ def cpu_oracle_sample(n: int, b: int, q: int, kind: str, reps: int = 1):
     return randutv_flops(n, n, b, q) / best / 1e12, best, oracle.num_threads()
 
 
+def workload_config(args, m: int, n: int, F: float, world: int) -> dict:
+    """The `config` object of both arms: the single-matrix workload timed."""
+    return {"workload": "randUTV %s %dx%d, %s spectrum, b=%d, %s, U and V formed" %
+                        (args.prec.upper(), m, n, args.spectrum, args.b,
+                         "learned q (fallback q=%d)" % args.q if args.learnedq else "q=%d" % args.q),
+            "m": m, "n": n, "b": args.b, "q": args.q, "spectrum": args.spectrum, "precision": args.prec,
+            "flops_per_factorization": F,
+            "l2": "inputs larger than L2 (A, T, U, V are %.2f GB each at m = n)" % (8e-9 * m * n),
+            "parallelism": "replicas x%d" % world}
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -179,8 +190,8 @@ def run_reference(args, rank: int, world: int):
         "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "randUTV FP64 %dx%d sample of the %dx%d workload" % (n_s, n_s, args.n, args.n),
-                   "m": n_s, "n": n_s, "b": args.b, "q": args.q, "spectrum": args.spectrum},
+        "config": workload_config(args, args.m if args.m > 0 else args.n, args.n,
+                                  randutv_flops(args.m if args.m > 0 else args.n, args.n, args.b, args.q), world),
         "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -442,13 +453,7 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "s_per_factorization": ms_per_step / 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.prec], "data": "synthetic",
-            "config": {"workload": "randUTV %s %dx%d, %s spectrum, b=%d, %s, U and V formed" %
-                       (args.prec.upper(), m, n, args.spectrum, b,
-                        "learned q (fallback q=%d)" % q if args.learnedq else "q=%d" % q),
-                       "m": m, "n": n, "b": b, "q": q, "spectrum": args.spectrum, "precision": args.prec,
-                       "flops_per_factorization": F,
-                       "l2": "inputs larger than L2 (A, T, U, V are 2.05 GB each)",
-                       "parallelism": "replicas x%d" % world},
+            "config": workload_config(args, m, n, F, world),
             "fp64_peak_tflops": fp64_peak,
             "pct_of_fp64_peak": 100.0 * (value / world) / fp64_peak,
             "vs_plain_fp64": compare,
