@@ -25,38 +25,48 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _i64 = ctypes.c_int64
 
 
+def compile_source(src: str, out: str) -> None:
+    """gcc -O2 -fopenmp of one C source into the shared library ``out``."""
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (plain gcc, OpenMP)."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
-    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
+    compile_source(_SRC, _LIB_PATH)
     return _LIB_PATH
+
+
+def bind(path: str):
+    """Load a library built from the oracle's C source and declare its signatures."""
+    lib = ctypes.CDLL(path)
+    lib.oracle_philox4x64_10.argtypes = [ctypes.POINTER(ctypes.c_uint64)] * 3
+    lib.oracle_gaussian.argtypes = [ctypes.c_uint64, _i64, _i64, _i64, _dp, _i64]
+    lib.oracle_gemm.argtypes = [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, ctypes.c_double,
+                                _dp, _i64, _dp, _i64, ctypes.c_double, _dp, _i64]
+    lib.oracle_householder_qr.argtypes = [_i64, _i64, _dp, _i64, _dp]
+    lib.oracle_larft.argtypes = [_i64, _i64, _dp, _i64, _dp, _dp, _i64]
+    lib.oracle_jacobi_svd.argtypes = [_i64, _dp, _i64, _dp, _dp, _i64, _dp, _i64, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_jacobi_svd.restype = ctypes.c_int
+    lib.oracle_randutv.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, ctypes.c_uint64,
+                                   _dp, _dp, _dp, _i64, ctypes.c_int]
+    lib.oracle_randutv.restype = ctypes.c_int
+    lib.oracle_num_threads.restype = ctypes.c_int
+    return lib
 
 
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            lib.oracle_philox4x64_10.argtypes = [ctypes.POINTER(ctypes.c_uint64)] * 3
-            lib.oracle_gaussian.argtypes = [ctypes.c_uint64, _i64, _i64, _i64, _dp, _i64]
-            lib.oracle_gemm.argtypes = [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, ctypes.c_double,
-                                        _dp, _i64, _dp, _i64, ctypes.c_double, _dp, _i64]
-            lib.oracle_householder_qr.argtypes = [_i64, _i64, _dp, _i64, _dp]
-            lib.oracle_larft.argtypes = [_i64, _i64, _dp, _i64, _dp, _dp, _i64]
-            lib.oracle_jacobi_svd.argtypes = [_i64, _dp, _i64, _dp, _dp, _i64, _dp, _i64, ctypes.c_int,
-                                              ctypes.POINTER(ctypes.c_int)]
-            lib.oracle_jacobi_svd.restype = ctypes.c_int
-            lib.oracle_randutv.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, ctypes.c_uint64,
-                                           _dp, _dp, _dp, _i64, ctypes.c_int]
-            lib.oracle_randutv.restype = ctypes.c_int
-            lib.oracle_num_threads.restype = ctypes.c_int
-            _lib = lib
+            _lib = bind(build())
     return _lib
 
 
