@@ -7,7 +7,9 @@
 // |a_p^T a_q| > tol sqrt(|a_p|^2 |a_q|^2), tol = w 2^-53, by the rotation that
 // makes them orthogonal (zeta = (beta - alpha) / (2 gamma),
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t).
-// Sweeps stop when no pair is rotated (cap: max_sweeps, else ST_NOCONV).
+// Sweeps stop when no pair is rotated (cap: max_sweeps, else ST_NOCONV);
+// k_jacobi_cluster also stops after a sweep whose couplings and rotation
+// angles were all tiny, when the next sweep would rotate nothing.
 // Output is canonical: singular values descending (stable on ties), columns of
 // Us = a_j / |a_j| (Gram-Schmidt completion for zero values), and each pair
 // negated when the entry of largest modulus of Vs(:, j) (lowest index on
