@@ -85,7 +85,9 @@ randutv_status randutv_factor(int64_t m, int64_t n, const double* A, int64_t lda
 
 /*
  * randutv_factor_ex -- randutv_factor with every option.
- *   prec       : precision of the sketch (randutv_precision); everything else is FP64.
+ *   prec       : precision variant (randutv_precision): which products run in
+ *                FP64, emulated FP64 or a lower precision.  Panel QRs, T factors
+ *                and the b x b SVD are FP64 in every variant.
  *   stream     : cudaStream_t to run on (NULL = legacy default stream).
  *   workspace  : device workspace of ws_bytes bytes (see randutv_workspace_size),
  *                or NULL to use the library's cached per-device workspace.
@@ -110,7 +112,7 @@ size_t randutv_workspace_size(int64_t m, int64_t n, int b, int prec);
  * randutv_factor_host -- randutv_factor on HOST buffers: copies A to the device,
  * factors it, copies U, T, V back (U or V NULL skips that factor).  A (lda >= m),
  * U (m x m), T (m x n), V (n x n) are host pointers, column-major; page-locked
- * (pinned) host memory gives full copy bandwidth.  The device copies of A/T, U
+ * (pinned) host memory avoids a staging copy.  The device copies of A/T, U
  * and V live in buffers the library caches per device and grows as needed
  * (like the workspace), so repeated calls do not allocate; calls on one device
  * must therefore not overlap (from several host threads).  Synchronous.
