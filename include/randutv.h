@@ -26,6 +26,11 @@
  *    Philox4x64-10(counter = (r/4, c, i, 0), key = (seed, 0)), so results are
  *    a deterministic function of (A, b, q, seed, precision); no atomics take
  *    part in any floating-point sum.
+ *  - Concurrent calls on one device (several host threads, several streams)
+ *    need distinct workspaces; the cached workspace (workspace == NULL) and
+ *    the host entry point's cached buffers are shared per device.  Each call
+ *    holds a per-device lock while it launches its work, because calls share
+ *    the library's side stream; the launched work still overlaps on the GPU.
  *  - Errors detected on the host return at once, before any launch.  Errors
  *    detected on the device (non-finite input, a Jacobi sweep cap, a bounded
  *    wait that ran out) are OR-ed into a device status word and reported

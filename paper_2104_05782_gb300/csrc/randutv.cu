@@ -303,6 +303,13 @@ cudaError_t side_stream(SideStream** out) {
     return cudaSuccess;
 }
 
+// Calls on one device share its side stream and events, so their launch
+// sequences must not interleave: each call enqueues its whole factorization
+// under its device's lock.  The GPU work of calls on different streams still
+// overlaps.
+std::mutex g_enqueue_mu[64];
+std::mutex& enqueue_lock(int dev) { return g_enqueue_mu[(unsigned)dev % 64u]; }
+
 enum SketchMode { MODE_FIXED = 0, MODE_LEARNED = 1, MODE_TRACE = 2 };
 
 // Splits of the trailing matrix reused by the emulated products of one block
@@ -1053,7 +1060,10 @@ randutv_status factor_impl(int64_t m, int64_t n, const double* A, int64_t lda, i
         for (int64_t i = 0; i < nb; ++i) ma.q_used[i] = -1;
     }
     if (m == 0) return RANDUTV_OK;
-    if (run_factor(c, A, lda, stop_after) != cudaSuccess) return RANDUTV_ECUDA;
+    {
+        std::lock_guard<std::mutex> lk(enqueue_lock(dev));
+        if (run_factor(c, A, lda, stop_after) != cudaSuccess) return RANDUTV_ECUDA;
+    }
     if (ma.tr_count) *ma.tr_count = c.tr_count;
     if (info != nullptr) {
         if (cudaMemcpyAsync(info, c.w.status, sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
