@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "randUTV s/factorization & TFLOP/s at n=16000: mixed/learned-q vs FP64, % peak"
-# digit products per emulated FP64 product (8 digits, pairs s + t <= 9)
+# digit products per emulated FP64 product (8 digits, the pairs with s + t <= 7, 0-based)
 OZ_PAIRS = 36
 DTYPES = {"fp64": "f64", "bf16": "f64+bf16-sketch", "fp16": "f64+fp16-sketch",
           "emul": "f64 (products emulated on bf16 tensor cores)",
@@ -154,6 +154,95 @@ def cpu_oracle_sample(n: int, b: int, q: int, kind: str, reps: int = 1):
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
     return randutv_flops(n, n, b, q) / best / 1e12, best, oracle.num_threads()
+
+
+def blas_randutv(A, b: int, q: int, seed: int, gaussian, want_uv: bool = True):
+    """Blocked randUTV on the host's BLAS and LAPACK: the CPU comparison run.
+
+    It follows the steps of Sec. 3.2 in the Householder form the GPU library
+    uses, on one node: the same Gaussian draws (``gaussian(seed, step, rows,
+    cols)``), Householder QRs with LAPACK's sign rule (dgeqrf through numpy)
+    and their compact WY factor (Sec. 2.3), right WY updates over all m rows,
+    left WY updates, and the b x b SVD (LAPACK dgesdd) with the canonical sign
+    (the entry of largest modulus of each right singular vector positive).
+    Everything goes through numpy, so one BLAS thread pool serves every call
+    and the products use every core.  Returns (U, T, V); U and V are None when
+    want_uv is False.
+    """
+    import numpy as np
+
+    def fmm(X, Y):  # X @ Y in column-major order, so updates of T, U, V run contiguously
+        return (Y.T @ X.T).T
+
+    def hqr(X):  # Householder QR -> (W unit lower, Tf upper with Q = I - W Tf W^T, R)
+        h, tau = np.linalg.qr(X, mode="raw")
+        f = h.T
+        k = X.shape[1]
+        W = np.tril(f, -1)[:, :k] + np.eye(X.shape[0], k)
+        Gm = fmm(W.T, W)
+        Tf = np.zeros((k, k))
+        for j in range(k):
+            Tf[:j, j] = -tau[j] * (Tf[:j, :j] @ Gm[:j, j])
+            Tf[j, j] = tau[j]
+        return np.asfortranarray(W), Tf, np.triu(f[:k, :k])
+
+    m, n = A.shape
+    T = np.array(A, dtype=np.float64, order="F")
+    U = np.eye(m, order="F") if want_uv else None
+    V = np.eye(n, order="F") if want_uv else None
+    k0, step = 0, 0
+    while k0 < n:
+        mp, np_ = m - k0, n - k0
+        if np_ > b:   # sketch step (Sec. 3.2.1) and right update with V_alpha
+            w = b
+            T22 = T[k0:, k0:]
+            Y = fmm(T22.T, gaussian(seed, step, mp, b))
+            for _ in range(q):
+                Y = fmm(T22.T, fmm(T22, Y))
+            W, Tf, _ = hqr(Y)
+            T[:, k0:] -= fmm(fmm(fmm(T[:, k0:], W), Tf), W.T)
+            if want_uv:
+                V[:, k0:] -= fmm(fmm(fmm(V[:, k0:], W), Tf), W.T)
+        else:         # final block: no sketch
+            w = np_
+        # panel QR (Sec. 3.2.2), left update of T22 and right update of U
+        W, Tf, R = hqr(T[k0:, k0:k0 + w])
+        if np_ > w:
+            C = T[k0:, k0 + w:]
+            C -= fmm(W, fmm(Tf.T, fmm(W.T, C)))
+        if want_uv:
+            U[:, k0:] -= fmm(fmm(fmm(U[:, k0:], W), Tf), W.T)
+        # b x b SVD (Sec. 3.2.3), canonical sign, and its application
+        Us, D, VsT = np.linalg.svd(R)
+        Vs = VsT.T
+        piv = np.argmax(np.abs(Vs), axis=0)
+        sgn = np.where(Vs[piv, np.arange(w)] < 0.0, -1.0, 1.0)
+        Us, Vs = Us * sgn, Vs * sgn
+        if k0 > 0:
+            T[:k0, k0:k0 + w] = fmm(T[:k0, k0:k0 + w], Vs)
+        if np_ > w:
+            T[k0:k0 + w, k0 + w:] = fmm(Us.T, T[k0:k0 + w, k0 + w:])
+        T[k0:, k0:k0 + w] = 0.0
+        T[k0:k0 + w, k0:k0 + w] = np.diag(D)
+        if want_uv:
+            V[:, k0:k0 + w] = fmm(V[:, k0:k0 + w], Vs)
+            U[:, k0:k0 + w] = fmm(U[:, k0:k0 + w], Us)
+        k0 += w
+        step += 1
+    return U, T, V
+
+
+def cpu_blas_sample(n: int, b: int, q: int, kind: str):
+    """Time blas_randutv on one n x n sample of the workload -> (TFLOP/s, seconds, cores)."""
+    import oracle
+    import synthetic
+
+    A = synthetic.test_matrix(n, n, kind, 1, 2)
+    oracle.build()
+    t0 = time.perf_counter()
+    blas_randutv(A, b, q, 0, oracle.gaussian)
+    dt = time.perf_counter() - t0
+    return randutv_flops(n, n, b, q) / dt / 1e12, dt, len(os.sched_getaffinity(0))
 
 
 def workload_config(args, m: int, n: int, F: float, world: int) -> dict:
@@ -439,13 +528,23 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
                "steps": E2E_STEPS, "warmup": 1,
                "api": "randutv_factor_host (pinned host buffers; H2D of A and D2H of U, T, V inside every timed call)"}
 
-    cpu = None
+    cpu = cpu_blas = None
     if rank == 0 and world == 1 and not args.no_cpu:
         n_s = 2048
         val, secs, cores = cpu_oracle_sample(n_s, b, q, args.spectrum)
         cpu = {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                "sample": "one %dx%d %s-spectrum factorization (b=%d, q=%d, U and V formed), %.1f s; "
                          "TFLOP/s from the same flop formula" % (n_s, n_s, args.spectrum, b, q, secs)}
+        # the same method on the host's BLAS and LAPACK (a comparison run, not the checker)
+        n_b = 4096
+        try:
+            bval, bsecs, bcores = cpu_blas_sample(n_b, b, q, args.spectrum)
+            cpu_blas = {"value": bval, "unit": "TFLOP/s", "cores": bcores,
+                        "kind": "blocked randUTV on numpy's BLAS/LAPACK (bench.blas_randutv)",
+                        "sample": "one %dx%d %s-spectrum factorization (b=%d, q=%d, U and V formed), %.1f s"
+                                  % (n_b, n_b, args.spectrum, b, q, bsecs)}
+        except Exception as exc:  # report, never lose the bench line over the comparison run
+            cpu_blas = {"error": "%s: %s" % (type(exc).__name__, exc)}
 
     if rank == 0:
         line = {
@@ -460,6 +559,7 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
             "quality_vs_reference": ref_quality,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "cpu_baseline_blas": cpu_blas,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
