@@ -699,6 +699,8 @@ def main():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     args = p.parse_args()
+    if args.workload == "single" and args.prec == "fp32":
+        p.error("--prec fp32 (the FP32 sketch) applies to --workload batched only")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
