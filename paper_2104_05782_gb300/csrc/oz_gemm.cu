@@ -10,8 +10,9 @@
 // |a_s| <= 127 (exact in BF16), each column c of op(B) likewise; then
 //   (op(A) op(B))(r,c) = 2^{eA_r + eB_c} sum_d 2^{-7d} sum_{s+t=d} (a_s b_t^T)(r,c).
 // With S = 8 digits (56 bits) and the digit pairs s + t <= S + 1 kept, the
-// error is about K 2^{-56} max|op(A)(r,:)| max|op(B)(:,c)| (digit truncation;
-// the dropped pairs weigh 2^{-70}).  One tcgen05 accumulator per digit sum d
+// truncation error is below 9.06 K 2^{-56} 2^{eA_r + eB_c} (the dropped pairs
+// weigh 2^{-70} each), and the double-float fold adds at most
+// 72 ceil(K / 128) 2^{-48} sum_k |a_k b_k|.  One tcgen05 accumulator per digit sum d
 // lives in TMEM (8 x 32 FP32 columns per 128 x 32 output tile, two buffers);
 // every 128 of K the partial sums are exact integers in FP32 (<= 8 pairs x
 // 128 x 127^2 < 2^24), and they are folded into double-float (hi, lo) FP32
