@@ -42,3 +42,27 @@ def test_blas_randutv_t_only():
 def test_cpu_blas_sample_reports_a_rate():
     val, secs, cores = bench.cpu_blas_sample(256, 32, 1, "gap")
     assert val > 0 and secs > 0 and cores >= 1
+
+
+def test_diag_quality_reports_the_spread_beside_the_median():
+    """A run of repeated sigma found exactly can hold the median of
+    T_ii / sigma_i at 1 while the other ratios spread by percents."""
+    n, b = 1000, 100
+    sigma = np.concatenate([np.ones(100), np.geomspace(1e-3, 1e-12, n - 100)])
+    r = np.concatenate([np.ones(100), 1 + 0.03 * np.where(np.arange(n - 100) % 2, 1, -1)])
+    q = bench.diag_quality(r * sigma, sigma, b)
+    assert q["Tii_over_sigma_median"] == 1.0
+    assert abs(q["Tii_over_sigma_median_abs_dev"] - 0.03) < 1e-12
+    assert q["Tii_within_5pct_of_sigma"] == 1.0
+    assert q["Tii_over_sigma_first_block_max_dev"] == 0.0
+
+
+def test_diag_quality_of_the_cpu_run_on_the_gap_spectrum():
+    """randUTV's own rank-revealing quality on the gap spectrum (q = 2): the
+    sigma = 1 block exactly, the decaying part within a few percent."""
+    n, b = 2048, 128          # the sigma = 1 cluster (n / 10) fills the first block
+    A = synthetic.test_matrix(n, n, "gap", 1, 2)
+    _, T, _ = bench.blas_randutv(A, b, 2, 0, oracle.gaussian, want_uv=False)
+    q = bench.diag_quality(np.abs(np.diag(T)), synthetic.spectrum("gap", n), b)
+    assert q["Tii_over_sigma_first_block_max_dev"] <= 1e-13
+    assert q["Tii_over_sigma_median_abs_dev"] <= 0.1
