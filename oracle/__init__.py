@@ -13,4 +13,5 @@ from .oracle import (  # noqa: F401
     num_threads,
     philox4x64_10,
     randutv,
+    randutv_qrfirst,
 )

@@ -58,6 +58,9 @@ def bind(path: str):
     lib.oracle_randutv.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, ctypes.c_uint64,
                                    _dp, _dp, _dp, _i64, ctypes.c_int]
     lib.oracle_randutv.restype = ctypes.c_int
+    lib.oracle_randutv_qrfirst.argtypes = [_i64, _i64, _dp, _i64, _i64, _i64, ctypes.c_uint64,
+                                           _dp, _dp, _dp, _i64, ctypes.c_int]
+    lib.oracle_randutv_qrfirst.restype = ctypes.c_int
     lib.oracle_num_threads.restype = ctypes.c_int
     return lib
 
@@ -161,4 +164,20 @@ def randutv(A, b: int, q: int, seed: int, want_uv: bool = True, stop_after: int 
                                 stop_after, max_sweeps)
     if rc < 0:
         raise ValueError("oracle_randutv: invalid arguments")
+    return U, T, V, rc
+
+
+def randutv_qrfirst(A, b: int, q: int, seed: int, want_uv: bool = True, stop_after: int = -1,
+                    max_sweeps: int = 30):
+    """randUTV with a Householder QR first (Sec. 5.1, tall inputs): A = Q_A [R; 0],
+    R = U_R T_R V^T, U = Q_A diag(U_R, I) -> (U, T, V, status)."""
+    A = _fortran(A)
+    m, n = A.shape
+    T = np.zeros((m, n), order="F")
+    U = np.zeros((m, m), order="F") if want_uv else None
+    V = np.zeros((n, n), order="F") if want_uv else None
+    rc = _load().oracle_randutv_qrfirst(m, n, _ptr(A), max(m, 1), b, q, seed, _ptr(U), _ptr(T), _ptr(V),
+                                        stop_after, max_sweeps)
+    if rc < 0:
+        raise ValueError("oracle_randutv_qrfirst: invalid arguments")
     return U, T, V, rc

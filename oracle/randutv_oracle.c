@@ -471,6 +471,56 @@ int oracle_randutv(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b
     return status;
 }
 
+/* ------------------------------------------------------------------------- */
+/* randUTV with a QR first, for tall inputs (Sec. 5.1: when m is much larger  */
+/* than n the input is first reduced by an unpivoted QR and randUTV runs on   */
+/* the n x n triangular factor).                                              */
+/*   A = Q_A [R; 0]   (HQR of A, Sec. 2.2, the dlarfg rule as above),         */
+/*   R = U_R T_R V^T  (oracle_randutv on the n x n R, same b, q, seed),      */
+/*   T = [T_R; 0],  V = V,  U = Q_A diag(U_R, I_{m-n}).                       */
+/* U is formed from its definition: X := diag(U_R, I), then the reflectors    */
+/* H_j = I - tau_j v_j v_j^T (v_j = [0; 1; A(j+1:m, j)] of the QR storage)    */
+/* are applied from the left, X := H_j X, for j = n-1 down to 0, since        */
+/* Q_A = H_0 H_1 ... H_{n-1}.  U and/or V may be NULL; stop_after and         */
+/* max_sweeps are passed to the randUTV of R.  Same return values as          */
+/* oracle_randutv.                                                            */
+/* ------------------------------------------------------------------------- */
+int oracle_randutv_qrfirst(int64_t m, int64_t n, const double* A, int64_t lda, int64_t b, int64_t q,
+                           uint64_t seed, double* U, double* T, double* V, int64_t stop_after, int max_sweeps) {
+    if (m < n || n < 0 || b < 1 || q < 0 || lda < m) return -1;
+    double* F = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1) * (size_t)(n > 0 ? n : 1));
+    double* tau = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double* R = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(n > 0 ? n : 1));
+    double* TR = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(n > 0 ? n : 1));
+    double* UR = U ? (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(n > 0 ? n : 1)) : NULL;
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i) F[IDX(i, j, m)] = A[IDX(i, j, lda)];
+    oracle_householder_qr(m, n, F, m, tau);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < n; ++i) R[IDX(i, j, n)] = (i <= j) ? F[IDX(i, j, m)] : 0.0;
+    int status = oracle_randutv(n, n, R, n, b, q, seed, UR, TR, V, stop_after, max_sweeps);
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i) T[IDX(i, j, m)] = (i < n) ? TR[IDX(i, j, n)] : 0.0;
+    if (U) {
+        for (int64_t j = 0; j < m; ++j)
+            for (int64_t i = 0; i < m; ++i)
+                U[IDX(i, j, m)] = (i < n && j < n) ? UR[IDX(i, j, n)] : (i == j && i >= n ? 1.0 : 0.0);
+        for (int64_t j = n - 1; j >= 0; --j) {
+            if (tau[j] == 0.0) continue;
+#pragma omp parallel for schedule(static)
+            for (int64_t c = 0; c < m; ++c) {
+                double s = U[IDX(j, c, m)];
+                for (int64_t r = j + 1; r < m; ++r) s += F[IDX(r, j, m)] * U[IDX(r, c, m)];
+                s *= tau[j];
+                U[IDX(j, c, m)] -= s;
+                for (int64_t r = j + 1; r < m; ++r) U[IDX(r, c, m)] -= s * F[IDX(r, j, m)];
+            }
+        }
+    }
+    free(F); free(tau); free(R); free(TR); free(UR);
+    return status;
+}
+
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
 int oracle_num_threads(void) {
 #ifdef _OPENMP

@@ -50,6 +50,11 @@ def _sketch():
     pins.test_randutv_power_iteration_sharpens_gap_spectrum()
 
 
+def _qrfirst():
+    pins.test_randutv_qrfirst_against_lapack_qr_and_identities(300, 100, 16, 1, "geometric10")
+    pins.test_randutv_qrfirst_against_lapack_qr_and_identities(160, 40, 12, 2, "normal")
+
+
 # (what the mistake is, text in the oracle, its replacement, pins that must see it)
 MUTANTS = [
     ("Philox key schedule constants swapped", "k0 += W0; k1 += W1;", "k0 += W1; k1 += W0;", _philox),
@@ -84,6 +89,12 @@ MUTANTS = [
     ("columns above the block not multiplied by Vs", "    if (k0 > 0) {\n        double* X", "    if (0) {\n        double* X",
      _utv),
     ("U not multiplied by Us", "U[IDX(i, k0 + j, m)] = X[IDX(i, j, m)];", "(void)X;", _utv),
+    ("QR-first: reflectors applied to U in the wrong order", "for (int64_t j = n - 1; j >= 0; --j) {",
+     "for (int64_t j = 0; j < n; ++j) {", _qrfirst),
+    ("QR-first: the pivot row of a reflector not updated", "                U[IDX(j, c, m)] -= s;\n", "\n",
+     _qrfirst),
+    ("QR-first: randUTV run on A instead of R", "int status = oracle_randutv(n, n, R, n, b, q, seed, UR, TR, V,",
+     "int status = oracle_randutv(n, n, F, m, b, q, seed, UR, TR, V,", _qrfirst),
 ]
 
 
@@ -107,7 +118,7 @@ def _rejected(check) -> bool:
 def test_unchanged_copy_passes_the_pins(tmp_path, monkeypatch):
     with open(SRC) as f:
         _load_copy(tmp_path, "same", f.read(), monkeypatch)
-    for check in (_philox, _gaussian, _hqr, _larft, _jacobi, _utv, _sketch):
+    for check in (_philox, _gaussian, _hqr, _larft, _jacobi, _utv, _sketch, _qrfirst):
         check()
 
 

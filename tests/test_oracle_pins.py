@@ -281,6 +281,50 @@ def test_randutv_t_only_mode_matches():
     assert np.array_equal(T1, T2)
 
 
+@pytest.mark.parametrize("m,n,b,q,kind", [
+    (300, 100, 16, 1, "geometric10"),   # m = 3n, b does not divide n
+    (160, 40, 12, 2, "normal"),          # m = 4n
+    (64, 64, 16, 1, "normal"),           # square: the QR is of a square matrix
+    (90, 30, 40, 1, "normal"),           # b >= n: the SVD of R
+])
+def test_randutv_qrfirst_against_lapack_qr_and_identities(m, n, b, q, kind):
+    """QR first (Sec. 5.1): T must be [T_R; 0] where T_R is randUTV of the R
+    factor of A, here taken from LAPACK's dgeqrf (an independent QR with the
+    same sign rule), and (U, T, V) must be a UTV factorization of A."""
+    from scipy.linalg import lapack
+
+    A = synthetic.test_matrix(m, n, kind, 21, 22)
+    nrm = np.linalg.norm(A)
+    U, T, V, rc = oracle.randutv_qrfirst(A, b, q, seed=3)
+    assert rc == 0
+    _check_utv(A, U, T, V)
+    qr, _, _, info = lapack.dgeqrf(np.asfortranarray(A))
+    assert info == 0
+    R = np.triu(qr[:n, :n])
+    UR, TR, VR, _ = oracle.randutv(R, b, q, 3)
+    assert np.abs(T[:n] - TR).max() <= 1e-10 * nrm
+    assert np.array_equal(T[n:], np.zeros((m - n, n)))
+    assert np.abs(T @ V.T - np.vstack([TR @ VR.T, np.zeros((m - n, n))])).max() <= 1e-10 * nrm
+    # U^T A = T V^T by definition of the factorization
+    assert np.abs(U.T @ A - T @ V.T).max() <= 50 * m * EPS * nrm
+    if b >= n:
+        s = np.linalg.svd(A, compute_uv=False)
+        assert np.abs(np.diag(T) - s).max() <= 1e-13 * s[0]
+
+
+def test_randutv_qrfirst_t_only_and_stop():
+    A = synthetic.test_matrix(200, 60, "normal", 5, 6)
+    U, T, V, _ = oracle.randutv_qrfirst(A, 16, 1, seed=2, want_uv=False)
+    assert U is None and V is None
+    _, T2, _, _ = oracle.randutv_qrfirst(A, 16, 1, seed=2)
+    assert np.array_equal(T, T2)
+    U, T, V, _ = oracle.randutv_qrfirst(A, 16, 1, seed=2, stop_after=2)
+    _check_utv(A, U, T, V, triangular=False)
+    assert np.array_equal(np.tril(T[:, :32], -1), np.zeros((200, 32)))
+    with pytest.raises(ValueError):
+        oracle.randutv_qrfirst(np.zeros((3, 5)), 2, 1, 0)
+
+
 def test_randutv_rejects_bad_arguments():
     with pytest.raises(ValueError):
         oracle.randutv(np.zeros((3, 5)), 2, 1, 0)  # m < n
