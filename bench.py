@@ -262,15 +262,55 @@ def diag_quality(d, sigma, b: int) -> dict:
             "Tii_over_sigma_first_block_max_dev": float(dev[:b].max())}
 
 
+# The CPU oracle arm (--impl reference) times a bounded sample of the workload
+# per step: the same spectrum, b and q at this size.
+REF_SAMPLE_N = 1536
+
+
+def diag_vs_plain(d_run, d_64, sigma) -> dict:
+    """Index-by-index comparison of two diagonals of T for the same matrix and seed.
+
+    r_i = |T_ii| / sigma_i of the timed run against the plain FP64 run.  An
+    index passes when r_i is within 5% of the FP64 ratio, or closer to 1 than
+    it.  Only sigma_i above the FP64 noise floor 1e3 2^-53 sigma_1 count (below
+    it both diagonals are rounding).  Indices that fail are listed (up to 20).
+    """
+    import numpy as np
+
+    d_run = np.asarray(d_run, dtype=np.float64)
+    d_64 = np.asarray(d_64, dtype=np.float64)
+    sg = np.asarray(sigma, dtype=np.float64) if sigma is not None else d_64
+    keep = sg > 1e3 * 2.0 ** -53 * sg[0]
+    idx = np.nonzero(keep)[0]
+    r_run, r_64 = d_run[keep] / sg[keep], d_64[keep] / sg[keep]
+    dev = np.abs(r_run / r_64 - 1.0)
+    ok = (dev <= 0.05) | (np.abs(np.log(r_run)) <= np.abs(np.log(r_64)))
+    bad = idx[~ok]
+    return {"indices_compared": int(keep.sum()), "noise_floor": "sigma_i > 1e3 2^-53 sigma_1",
+            "max_dev": float(dev.max()) if dev.size else None,
+            "median_dev": float(np.median(dev)) if dev.size else None,
+            "frac_within_5pct": float((dev <= 0.05).mean()) if dev.size else None,
+            "frac_within_5pct_or_closer_to_sigma": float(ok.mean()) if dev.size else None,
+            "failing_indices": [{"i": int(i), "sigma": float(sg[i]), "Tii": float(d_run[i]),
+                                 "Tii_fp64": float(d_64[i])} for i in bad[:20]],
+            "failing_count": int(bad.size)}
+
+
 def workload_config(args, m: int, n: int, F: float, world: int) -> dict:
-    """The `config` object of both arms: the single-matrix workload timed."""
-    return {"workload": "randUTV %s %dx%d, %s spectrum, b=%d, %s, U and V formed" %
+    """The `config` object of both arms: the single-matrix workload timed.
+
+    Both arms print the same object; `reference_sample` states the size the
+    CPU oracle arm actually factors per step."""
+    return {"workload": "randUTV %s %dx%d, %s spectrum, b=%d, %s, U and V formed%s" %
                         (args.prec.upper(), m, n, args.spectrum, args.b,
-                         "learned q (fallback q=%d)" % args.q if args.learnedq else "q=%d" % args.q),
+                         "learned q (fallback q=%d)" % args.q if args.learnedq else "q=%d" % args.q,
+                         ", Householder QR first" if getattr(args, "qr_first", False) else ""),
             "m": m, "n": n, "b": args.b, "q": args.q, "spectrum": args.spectrum, "precision": args.prec,
             "flops_per_factorization": F,
             "l2": "inputs larger than L2 (A, T, U, V are %.2f GB each at m = n)" % (8e-9 * m * n),
-            "parallelism": "replicas x%d" % world}
+            "parallelism": "replicas x%d" % world,
+            "reference_sample": "the CPU oracle arm factors a %dx%d sample of this workload (same spectrum, b, q) "
+                                "per step, not the full size" % (REF_SAMPLE_N, REF_SAMPLE_N)}
 
 
 def run_reference(args, rank: int, world: int):
@@ -279,7 +319,7 @@ def run_reference(args, rank: int, world: int):
     import oracle
     import synthetic
 
-    n_s = 1536
+    n_s = REF_SAMPLE_N
     A = synthetic.test_matrix(n_s, n_s, args.spectrum, 1, 2)
     oracle.build()
     for _ in range(args.warmup):
@@ -298,6 +338,8 @@ def run_reference(args, rank: int, world: int):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args, args.m if args.m > 0 else args.n, args.n,
                                   randutv_flops(args.m if args.m > 0 else args.n, args.n, args.b, args.q), world),
+        "sample": {"m": n_s, "n": n_s, "b": args.b, "q": args.q, "spectrum": args.spectrum,
+                   "flops_per_factorization": F},
         "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -357,9 +399,16 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
     T = rutv.colmajor_empty(m, n, dev)
     U = rutv.colmajor_empty(m, m, dev)
     V = rutv.colmajor_empty(n, n, dev)
-    ws_bytes = rutv.randutv_workspace_size(m, n, b, prec)
-    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    opt = None
+    if args.qr_first:
+        opt = rutv.randutv_options(prec=prec, stream=stream, qr_first=True)
+        ws_bytes = rutv.randutv_workspace_size_opt(m, n, b, opt)
+    else:
+        ws_bytes = rutv.randutv_workspace_size(m, n, b, prec)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+    if opt is not None:
+        opt.workspace, opt.ws_bytes = ws.data_ptr(), ws_bytes
 
     qnet = rutv.load_qnet() if args.learnedq else None
     q_used = []
@@ -368,6 +417,8 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
         if args.learnedq:
             st, qu = rutv.randutv_factor_learnedq(m, n, A, m, b, qnet, 0, U, T, V, prec=prec, stream=stream)
             q_used[:] = qu
+        elif opt is not None:
+            st = rutv.randutv_factor_opt(m, n, A, m, b, q, 0, U, T, V, opt)
         else:
             st = rutv.randutv_factor_ex(m, n, A, m, b, q, 0, U, T, V, prec, stream, ws, ws_bytes, -1, None)
         if st != rutv.RANDUTV_OK:
@@ -408,6 +459,7 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
 
     # quality of this run (not timed): diagonal of T against the prescribed spectrum
     d = torch.diagonal(T).abs().cpu().numpy()
+    d_primary = d.copy()
     quality = None
     if sigma is not None:
         quality = diag_quality(d, sigma, b)
@@ -442,8 +494,7 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
             "bound": "tensor", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
             "frac": (achieved / fp64_peak) if achieved else None,
             # DRAM bytes per flop of one ncu-captured launch of this kernel (the
-            # 4096^2 rank-128 update, profiles/gemm_f64_rank128_4096.md) times the
-            # average flops of a launch here
+            # 4096^2 rank-128 update) times the average flops of a launch here
             "traffic": GEMM_F64_DRAM_BYTES_PER_FLOP * g_fl / max(g_launch, 1),
             "traffic_source": "ncu dram__bytes_read+write of k_gemm_f64 on the 4096^2 case (0.0518 B/flop), "
                               "scaled by the average flops per launch",
@@ -508,12 +559,32 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
         t64 = c0.elapsed_time(c1) / 1e3
         compare = {"path": "plain FP64 (DMMA products), same matrix, one timed run after the primary runs",
                    "s_per_factorization": t64, "tflops": F / t64 / 1e12,
-                   "speedup_of_primary": t64 / (ms_per_step / 1e3)}
+                   "speedup_of_primary": t64 / (ms_per_step / 1e3),
+                   "Tii_vs_plain_fp64": diag_vs_plain(d_primary, torch.diagonal(T).abs().cpu().numpy(), sigma)}
         del ws64
+
+    # QR first: the same precision without the QR, once, on the same matrix
+    vs_direct = None
+    if args.qr_first:
+        wsd_bytes = rutv.randutv_workspace_size(m, n, b, prec)
+        wsd = torch.empty(max(wsd_bytes, 1), dtype=torch.uint8, device=dev)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        c0.record(stream)
+        st = rutv.randutv_factor_ex(m, n, A, m, b, q, 0, U, T, V, prec, stream, wsd, wsd_bytes, -1, None)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        if st != rutv.RANDUTV_OK:
+            raise rutv.RandUTVError(st, "randutv_factor_ex (without the QR)")
+        td = c0.elapsed_time(c1) / 1e3
+        vs_direct = {"path": "the same precision without the QR first, one timed run",
+                     "s_per_factorization": td, "speedup_of_qr_first": td / (ms_per_step / 1e3)}
+        del wsd
 
     # end to end through the C ABI on HOST buffers (copies inside the timed region)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.qr_first:
         Ah = A.t().contiguous().cpu().pin_memory()   # row-major A^T == column-major A
         Th = torch.empty((n, m), dtype=torch.float64).pin_memory()
         Uh = torch.empty((m, m), dtype=torch.float64).pin_memory()
@@ -570,6 +641,7 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
             "fp64_peak_tflops": fp64_peak,
             "pct_of_fp64_peak": 100.0 * (value / world) / fp64_peak,
             "vs_plain_fp64": compare,
+            "vs_without_qr_first": vs_direct,
             "quality_vs_reference": ref_quality,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -703,6 +775,9 @@ def main():
                    help="also factor with this precision and report T_ii/sigma_i against it")
     p.add_argument("--learnedq", action="store_true",
                    help="primary path picks q per block with the shipped network (fixed q=2 timed beside it)")
+    p.add_argument("--qr-first", action="store_true",
+                   help="Householder QR of A first, then randUTV of its R (tall inputs); one timed "
+                        "factorization of the default path on the same matrix is reported beside it")
     p.add_argument("--b", type=int, default=128)
     p.add_argument("--q", type=int, default=2)
     p.add_argument("--spectrum", default="gap")

@@ -114,6 +114,79 @@ randutv_status randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t 
 size_t randutv_workspace_size(int64_t m, int64_t n, int b, int prec);
 
 /*
+ * randutv_options -- the variants of randutv_factor_opt, which randutv_factor_ex
+ * does not offer.  Initialise with randutv_options_init, then set fields.
+ *   prec, stream, workspace, ws_bytes : as randutv_factor_ex (the workspace
+ *                size comes from randutv_workspace_size_opt).
+ *   stop_after : stop after this many block steps of this call (< 0: none).
+ *   rank_tol   : > 0 stops at a tolerance (the early termination at rank k of
+ *                Sec. 1.1 and Sec. 3.2, whose cost is O(m n k)): after the
+ *                first block step whose smallest diagonal entry satisfies
+ *                |T_jj| <= rank_tol * |T_00| (T_00, the largest singular value
+ *                estimate, is the first entry of the first block).  The
+ *                result is a partial factorization A = U T V^T whose first
+ *                cols_done columns of T are upper triangular.  The host reads
+ *                each block's diagonal (one synchronisation per block step).
+ *   start_col  : > 0 resumes a partial factorization (from stop_after,
+ *                rank_tol or an earlier resume): T (m x n) holds it, its
+ *                first start_col columns upper triangular, and U, V (when not
+ *                NULL) hold its orthogonal factors, which are updated in
+ *                place; A is not read (may be NULL).  The block steps
+ *                continue with step index start_col / b (start_col must be a
+ *                multiple of b, <= n), so the Gaussian draws, and the result,
+ *                are those of one uninterrupted call.  Not with qr_first.
+ *   qr_first   : 1 = for tall inputs (Sec. 5.1): A = Q_A [R; 0] by blocked
+ *                Householder QR (panels of b columns, dlarfg rule, compact WY),
+ *                then randUTV of the n x n R = U_R T_R V^T, so that
+ *                T = [T_R; 0] and U = Q_A diag(U_R, I).
+ *   cols_done  : out: columns of T that are upper triangular on return.
+ *   rank       : out: with rank_tol > 0, the number of |T_jj| > rank_tol |T_00|
+ *                among those columns; else cols_done.
+ */
+typedef struct randutv_options {
+    int prec;
+    void* stream;
+    void* workspace;
+    size_t ws_bytes;
+    int64_t stop_after;
+    double rank_tol;
+    int64_t start_col;
+    int qr_first;
+    int64_t cols_done;
+    int64_t rank;
+} randutv_options;
+
+/* Defaults: RANDUTV_FP64, legacy stream, cached workspace, no stop, no
+ * tolerance, start_col 0, qr_first 0. */
+void randutv_options_init(randutv_options* opt);
+
+/* Bytes of device workspace randutv_factor_opt needs with these options. */
+size_t randutv_workspace_size_opt(int64_t m, int64_t n, int b, const randutv_options* opt);
+
+/*
+ * randutv_factor_opt -- randutv_factor_ex with the options above (opt may be
+ * NULL for the defaults).  Arguments as randutv_factor; synchronises the
+ * stream and returns the status.  RANDUTV_EINVAL also for start_col that is
+ * not a multiple of b or exceeds n, start_col with qr_first, or a negative
+ * rank_tol.
+ */
+randutv_status randutv_factor_opt(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q,
+                                  uint64_t seed, double* U, double* T, double* V, randutv_options* opt);
+
+/*
+ * randutv_set_limits -- process-wide limits of the device-side failure
+ * detection, for tests of those paths (the paper has no counterpart).
+ *   wait_polls : polls after which a grid barrier of the cooperative panel
+ *                and Jacobi kernels gives up and the call reports
+ *                RANDUTV_ETIMEOUT (each poll sleeps 64-256 ns); <= 0 restores
+ *                the default (2^23 polls, about a second).
+ *   max_sweeps : sweep cap of every b x b Jacobi SVD, after which the call
+ *                reports RANDUTV_ENOCONV; <= 0 restores the default (30).
+ * Takes effect for launches made after it returns; not for the batched path.
+ */
+void randutv_set_limits(int64_t wait_polls, int max_sweeps);
+
+/*
  * randutv_factor_host -- randutv_factor on HOST buffers: copies A to the device,
  * factors it, copies U, T, V back (U or V NULL skips that factor).  A (lda >= m),
  * U (m x m), T (m x n), V (n x n) are host pointers, column-major; page-locked
@@ -177,7 +250,8 @@ randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64
  * sketch of every block step, a small network (16 -> 64 -> 64 -> 4, GELU,
  * FP32, softmax over q in {0,1,2,3}) picks q from 16 features: the decay of
  * the previous block's diagonal and of the Householder R diagonal of the
- * q = 0 sketch, each as log10(|d_j| / |d_0|) at j = 0, w/8, ..., 7w/8.
+ * q = 0 sketch (compressed to 2b rows by a second Gaussian sketch, a
+ * subspace embedding), each as log10(|d_j| / |d_0|) at j = 0, w/8, ..., 7w/8.
  * The q = 0 product is reused by the chosen iterations.
  *   model   : HOST array of randutv_learnq_model_floats() floats (layout:
  *             W1[16][64] b1[64] W2[64][64] b2[64] W3[64][4] b3[4] mu[16] sd[16],
@@ -188,8 +262,12 @@ randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64
  *             probability reaches 0.95.
  *   q_used  : HOST array of ceil(n / b) ints (or NULL): the q chosen per
  *             sketch step, -1 for the final block (no sketch).
- * Other arguments as randutv_factor / randutv_factor_ex.  Synchronises the
- * stream once per block step to read the choice.
+ * Other arguments as randutv_factor / randutv_factor_ex.  The choice stays
+ * on the device: every power iteration up to q = 3 is queued, and its
+ * kernels return at once when the chosen q is smaller, so the host never
+ * waits for a block step; q_used is filled once, when the call ends.  Each
+ * block's b x b SVD overlaps the next step on a side stream, as in the
+ * fixed-q path; the next step's features wait only for its singular values.
  */
 int randutv_learnq_model_floats(void);
 randutv_status randutv_factor_learnedq(int64_t m, int64_t n, const double* A, int64_t lda, int b,
@@ -206,11 +284,22 @@ randutv_status randutv_factor_learnedq_ex(int64_t m, int64_t n, const double* A,
  * float[16] each), the label (HOST int: the smallest q in {0,1,2} whose
  * diagonal sigma(T22 Q1(q)) stays within 5% of the q = 2 one, entry by entry),
  * and optionally the four candidate diagonals (HOST double[4 * b] each).
+ * Diagonal entries below 1e-13 times the first block's largest are rounding
+ * noise and take no part in the label.
  * *nblocks receives the number of steps written.
  */
 randutv_status randutv_learnq_trace(int64_t m, int64_t n, const double* A, int64_t lda, int b, uint64_t seed,
                                     double* T, float* features, int* labels, double* candidates,
                                     int64_t max_blocks, int64_t* nblocks);
+/* As randutv_learnq_trace, with the products in `prec` (RANDUTV_FP64 or
+ * RANDUTV_FP64_EMULATED) and only every stride-th sketch step recorded (step
+ * 0 and the steps i with i % stride == seed % stride; the others run the q = 2
+ * step alone), which makes traces of many large matrices affordable.
+ * stride >= 1.  Labels skip diagonal entries below 1e-13 times the first
+ * block's largest (rounding noise); a block of noise alone is labelled 0. */
+randutv_status randutv_learnq_trace_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b, uint64_t seed,
+                                       double* T, float* features, int* labels, double* candidates,
+                                       int64_t max_blocks, int64_t* nblocks, int prec, int64_t stride);
 
 /*
  * Network training and evaluation on the GPU with the library's own kernels

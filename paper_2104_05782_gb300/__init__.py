@@ -40,6 +40,14 @@ class TraceClass(ctypes.Structure):
                 ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class Options(ctypes.Structure):
+    """randutv_options of the C ABI."""
+    _fields_ = [("prec", ctypes.c_int), ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("ws_bytes", ctypes.c_size_t), ("stop_after", ctypes.c_int64), ("rank_tol", ctypes.c_double),
+                ("start_col", ctypes.c_int64), ("qr_first", ctypes.c_int), ("cols_done", ctypes.c_int64),
+                ("rank", ctypes.c_int64)]
+
+
 class RandUTVError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -106,12 +114,26 @@ def load():
     lib.randutv_learnq_trace.argtypes = [_i64, _i64, _vp, _i64, ctypes.c_int, ctypes.c_uint64, _vp, fp, ip,
                                          ctypes.POINTER(ctypes.c_double), _i64, ctypes.POINTER(ctypes.c_int64)]
     lib.randutv_learnq_trace.restype = ctypes.c_int
+    lib.randutv_learnq_trace_ex.argtypes = [_i64, _i64, _vp, _i64, ctypes.c_int, ctypes.c_uint64, _vp, fp, ip,
+                                            ctypes.POINTER(ctypes.c_double), _i64, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.c_int, _i64]
+    lib.randutv_learnq_trace_ex.restype = ctypes.c_int
     lib.randutv_learnq_train.argtypes = [fp, ip, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float, fp, fp]
     lib.randutv_learnq_train.restype = ctypes.c_int
     lib.randutv_learnq_grad.argtypes = [fp, ip, ctypes.c_int, fp, fp, fp]
     lib.randutv_learnq_grad.restype = ctypes.c_int
     lib.randutv_learnq_predict.argtypes = [fp, fp, ctypes.c_int, fp]
     lib.randutv_learnq_predict.restype = ctypes.c_int
+    op = ctypes.POINTER(Options)
+    lib.randutv_options_init.argtypes = [op]
+    lib.randutv_options_init.restype = None
+    lib.randutv_workspace_size_opt.argtypes = [_i64, _i64, ctypes.c_int, op]
+    lib.randutv_workspace_size_opt.restype = ctypes.c_size_t
+    lib.randutv_factor_opt.argtypes = [_i64, _i64, _vp, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                       _vp, _vp, _vp, op]
+    lib.randutv_factor_opt.restype = ctypes.c_int
+    lib.randutv_set_limits.argtypes = [_i64, ctypes.c_int]
+    lib.randutv_set_limits.restype = None
     lib.randutv_svd_small_noalloc.argtypes = [ctypes.c_int, _vp, _i64, _vp, _vp, _vp, _vp]
     lib.randutv_svd_small_noalloc.restype = ctypes.c_int
     _lib = lib
@@ -152,6 +174,37 @@ def randutv_factor_ex(m, n, A, lda, b, q, seed, U, T, V, prec=RANDUTV_FP64, stre
     """randutv_factor_ex of the C ABI; returns the status."""
     return load().randutv_factor_ex(m, n, _ptr(A), lda, b, q, seed, _ptr(U), _ptr(T), _ptr(V), prec,
                                     _stream_handle(stream), _ptr(workspace), ws_bytes, stop_after, _ptr(info))
+
+
+def randutv_options(prec=RANDUTV_FP64, stream=None, workspace=None, ws_bytes=0, stop_after=-1, rank_tol=0.0,
+                    start_col=0, qr_first=False) -> Options:
+    """A randutv_options filled by randutv_options_init, then with these fields."""
+    o = Options()
+    load().randutv_options_init(ctypes.byref(o))
+    o.prec = prec
+    o.stream = _stream_handle(stream)
+    o.workspace = _ptr(workspace)
+    o.ws_bytes = ws_bytes
+    o.stop_after = stop_after
+    o.rank_tol = rank_tol
+    o.start_col = start_col
+    o.qr_first = 1 if qr_first else 0
+    return o
+
+
+def randutv_factor_opt(m, n, A, lda, b, q, seed, U, T, V, opt=None) -> int:
+    """randutv_factor_opt of the C ABI; opt (an Options or None) receives cols_done and rank."""
+    return load().randutv_factor_opt(m, n, _ptr(A), lda, b, q, seed, _ptr(U), _ptr(T), _ptr(V),
+                                     ctypes.byref(opt) if opt is not None else None)
+
+
+def randutv_workspace_size_opt(m, n, b, opt=None) -> int:
+    return int(load().randutv_workspace_size_opt(m, n, b, ctypes.byref(opt) if opt is not None else None))
+
+
+def randutv_set_limits(wait_polls: int, max_sweeps: int) -> None:
+    """randutv_set_limits of the C ABI (<= 0 restores a default)."""
+    load().randutv_set_limits(int(wait_polls), int(max_sweeps))
 
 
 def randutv_workspace_size(m, n, b, prec=RANDUTV_FP64) -> int:
@@ -283,8 +336,9 @@ def randutv_factor_learnedq(m, n, A, lda, b, model, seed, U, T, V, q_used=None, 
     return r, list(qu[:nb])
 
 
-def randutv_learnq_trace(m, n, A, lda, b, seed, T, max_blocks=None, candidates=False):
-    """randutv_learnq_trace of the C ABI -> (status, features (k x 16), labels (k,), candidates (k x 4 x b) or None)."""
+def randutv_learnq_trace(m, n, A, lda, b, seed, T, max_blocks=None, candidates=False, prec=None, stride=1):
+    """randutv_learnq_trace (or, with prec / stride, randutv_learnq_trace_ex) of the C ABI
+    -> (status, features (k x 16), labels (k,), candidates (k x 4 x b) or None)."""
     import numpy as np
     mb = max_blocks if max_blocks is not None else max(-(-n // b), 1)
     f, fp = _f32(np.zeros((mb, 16), dtype=np.float32))
@@ -292,7 +346,11 @@ def randutv_learnq_trace(m, n, A, lda, b, seed, T, max_blocks=None, candidates=F
     cand = np.zeros((mb, 4, b), dtype=np.float64) if candidates else None
     cp = cand.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if candidates else None
     cnt = ctypes.c_int64(0)
-    r = load().randutv_learnq_trace(m, n, _ptr(A), lda, b, seed, _ptr(T), fp, yp, cp, mb, ctypes.byref(cnt))
+    if prec is None and stride == 1:
+        r = load().randutv_learnq_trace(m, n, _ptr(A), lda, b, seed, _ptr(T), fp, yp, cp, mb, ctypes.byref(cnt))
+    else:
+        r = load().randutv_learnq_trace_ex(m, n, _ptr(A), lda, b, seed, _ptr(T), fp, yp, cp, mb, ctypes.byref(cnt),
+                                           RANDUTV_FP64 if prec is None else prec, stride)
     k = cnt.value
     return r, f[:k].copy(), y[:k].copy(), (cand[:k].copy() if candidates else None)
 
@@ -373,3 +431,32 @@ def factor(A, b: int, q: int, seed: int = 0, want_uv: bool = True, prec: int = R
     if check and st != RANDUTV_OK:
         raise RandUTVError(st, "randutv_factor_ex")
     return U, T, V
+
+
+def factor_opt(A, b: int, q: int, seed: int = 0, want_uv: bool = True, prec: int = RANDUTV_FP64, stream=None,
+               stop_after: int = -1, rank_tol: float = 0.0, qr_first: bool = False, check: bool = True):
+    """randutv_factor_opt on a column-major FP64 CUDA tensor -> (U, T, V, cols_done, rank)."""
+    m, n = A.shape
+    if not is_colmajor(A):
+        raise ValueError("A must be column-major (e.g. a transposed contiguous tensor)")
+    T = colmajor_empty(m, n, A.device)
+    U = colmajor_empty(m, m, A.device) if want_uv else None
+    V = colmajor_empty(n, n, A.device) if want_uv else None
+    lda = A.stride(1) if n > 1 else max(m, 1)
+    o = randutv_options(prec=prec, stream=stream, stop_after=stop_after, rank_tol=rank_tol, qr_first=qr_first)
+    st = randutv_factor_opt(m, n, A, max(lda, m, 1), b, q, seed, U, T, V, o)
+    if check and st != RANDUTV_OK:
+        raise RandUTVError(st, "randutv_factor_opt")
+    return U, T, V, int(o.cols_done), int(o.rank)
+
+
+def resume(U, T, V, b: int, q: int, seed: int, start_col: int, prec: int = RANDUTV_FP64, stream=None,
+           stop_after: int = -1, rank_tol: float = 0.0, check: bool = True):
+    """Continue the partial factorization held in (U, T, V) (column-major CUDA
+    tensors, updated in place) from column start_col -> (cols_done, rank)."""
+    m, n = T.shape
+    o = randutv_options(prec=prec, stream=stream, stop_after=stop_after, rank_tol=rank_tol, start_col=start_col)
+    st = randutv_factor_opt(m, n, None, max(m, 1), b, q, seed, U, T, V, o)
+    if check and st != RANDUTV_OK:
+        raise RandUTVError(st, "randutv_factor_opt (resume)")
+    return int(o.cols_done), int(o.rank)

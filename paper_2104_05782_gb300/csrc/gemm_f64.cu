@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(NTHREADS) k_gemm_f64(int M, int N, int K, doub
                                                        const double* __restrict__ A, int64_t lda,
                                                        const double* __restrict__ B, int64_t ldb,
                                                        double beta, double* __restrict__ C, int64_t ldc,
-                                                       double* __restrict__ P, int kchunk) {
+                                                       double* __restrict__ P, int kchunk, DevGate gate) {
+    if (gate_closed(gate)) return;
     __shared__ double As[BK][BM + APAD];
     __shared__ double Bs[BK][BN + BPAD];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -145,7 +146,8 @@ __global__ void __launch_bounds__(NTHREADS) k_gemm_f64(int M, int N, int K, doub
 
 // C = sum_z P[z] (fixed order z = 0..S-1) + beta * C.
 __global__ void k_splitk_reduce(int M, int N, int S, const double* __restrict__ P, double beta,
-                                double* __restrict__ C, int64_t ldc) {
+                                double* __restrict__ C, int64_t ldc, DevGate gate) {
+    if (gate_closed(gate)) return;
     int64_t total = (int64_t)M * N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -179,7 +181,7 @@ cudaError_t gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double a
     if (K <= 0) {  // C = beta * C
         if (beta == 1.0) return cudaSuccess;
         k_splitk_reduce<<<(unsigned)std::min<int64_t>(cdiv(M * N, 256), 4096), 256, 0, st>>>(
-            (int)M, (int)N, 0, partials, beta, C, ldc);
+            (int)M, (int)N, 0, partials, beta, C, ldc, current_gate());
         trace_count(1);
         return cudaGetLastError();
     }
@@ -199,7 +201,7 @@ cudaError_t gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double a
     dim3 block(NTHREADS);
 #define LAUNCH(TA_, TB_)                                                                             \
     k_gemm_f64<TA_, TB_><<<grid, block, 0, st>>>((int)M, (int)N, (int)K, alpha, A, lda, B, ldb, beta, \
-                                                 C, ldc, partials, kchunk)
+                                                 C, ldc, partials, kchunk, current_gate())
     if (!ta && !tb) LAUNCH(false, false);
     else if (ta && !tb) LAUNCH(true, false);
     else if (!ta && tb) LAUNCH(false, true);
@@ -210,7 +212,7 @@ cudaError_t gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double a
     if (e != cudaSuccess || S == 1) return e;
     int64_t total = M * N;
     unsigned blocks = (unsigned)std::min<int64_t>(cdiv(total, 256), 8LL * sms);
-    k_splitk_reduce<<<blocks, 256, 0, st>>>((int)M, (int)N, S, partials, beta, C, ldc);
+    k_splitk_reduce<<<blocks, 256, 0, st>>>((int)M, (int)N, S, partials, beta, C, ldc, current_gate());
     trace_count(1);
     return cudaGetLastError();
 }

@@ -9,6 +9,30 @@
 
 namespace rutv {
 
+// ---- launch gate of the product kernels (randutv.cu) -------------------------
+// The product, split and reduction launchers below pass the calling thread's
+// current gate (DevGate of common.cuh) to their kernels; a GateScope sets it
+// for the launches made during its lifetime.
+struct DevGate;
+const DevGate& current_gate();
+class GateScope {
+  public:
+    GateScope(const int* flag, int need);
+    ~GateScope();
+    GateScope(const GateScope&) = delete;
+    GateScope& operator=(const GateScope&) = delete;
+
+  private:
+    const int* saved_flag_;
+    int saved_need_;
+};
+
+// ---- process-wide limits of the device-side failure detection (randutv.cu) --
+// Polls after which a grid barrier gives up (ST_TIMEOUT), and the sweep cap
+// of the b x b Jacobi SVD (ST_NOCONV).  Defaults: kSpinLimit and 30.
+long long wait_limit();
+int sweep_cap();
+
 // ---- FP64 DMMA products (gemm_f64.cu) --------------------------------------
 // C = alpha op(A) op(B) + beta C (column-major).  partials (partial_elems
 // doubles) enables the deterministic split-K for skinny products; may be null.
@@ -58,6 +82,10 @@ cudaError_t copy_matrix(const double* src, int64_t lds, double* dst, int64_t ldd
 // Block column T(k0:m, k0:k0+w) := [diag(D); 0].
 cudaError_t set_diag_block(double* T, int64_t ldt, int64_t k0, int64_t m, int w, const double* D,
                            cudaStream_t st);
+// X(i, j) := 0 for i > j (rows x cols).
+cudaError_t zero_below_diag(double* X, int64_t ld, int64_t rows, int64_t cols, cudaStream_t st);
+// X (m x m) := diag(X(0:n, 0:n), I_{m-n}).
+cudaError_t embed_identity(double* X, int64_t ld, int64_t m, int64_t n, cudaStream_t st);
 // *status |= ST_NONFINITE if any entry of the rows x cols matrix X is not finite.
 cudaError_t check_finite(const double* X, int64_t ld, int64_t rows, int64_t cols, int* status,
                          cudaStream_t st);
@@ -82,9 +110,13 @@ cudaError_t cholqr32(float* X, int64_t L, int b, int passes, uint16_t* Xb, int64
 
 // ---- learned q (learnq.cu) --------------------------------------------------
 int learnq_nparam();
-cudaError_t learnq_features(const double* T, int64_t ldt, int64_t k0, int wprev, const double* R, int64_t ldr, int w,
+// Features of a block step from the previous block's diagonal (dprev[j * dstride],
+// j < wprev; wprev = 0 for the first block) and the QR storage R of the
+// compressed q = 0 sketch.
+cudaError_t learnq_features(const double* dprev, int64_t dstride, int wprev, const double* R, int64_t ldr, int w,
                             float* f, cudaStream_t st);
-cudaError_t learnq_infer(const float* P, const float* f, int fallback, int* q, cudaStream_t st);
+// q (device) := the network's choice; also written to *qlog when qlog != null.
+cudaError_t learnq_infer(const float* P, const float* f, int fallback, int* q, int* qlog, cudaStream_t st);
 size_t learnq_train_scratch_floats(int N);
 cudaError_t learnq_train_step(float* P, const float* X, const int* y, int N, float* scratch, float* grads_out,
                               float* loss_out, int t, float lr, float wd, cudaStream_t st);

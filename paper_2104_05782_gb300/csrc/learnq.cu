@@ -6,10 +6,14 @@
 // (mu, sd) stored in the model.  Parameter layout (row-major, x W):
 //   W1[16][64] b1[64] W2[64][64] b2[64] W3[64][4] b3[4] mu[16] sd[16]
 // Features of block step i (written by k_learnq_features):
-//   f[0..7]  = log10(|T_jj| / |T_00|) of the previous diagonal block at
-//              j = 0, w/8, ..., 7w/8 (block 0: copies of f[8..15]);
-//   f[8..15] = log10(|R_jj| / |R_00|) of the Householder R of the q = 0
-//              sketch Y0 = T22^T G at the same j.
+//   f[0..7]  = log10(|d_j| / |d_0|) of the previous diagonal block d (the
+//              singular values its b x b SVD produced) at j = 0, w/8, ...,
+//              7w/8 (block 0: copies of f[8..15]);
+//   f[8..15] = log10(|R_jj| / |R_00|) at the same j, with R the Householder
+//              R of the q = 0 sketch Y0 = T22^T G compressed to at most 2b
+//              rows by a second Gaussian sketch (Omega Y0, Omega 2b x n'; a
+//              subspace embedding, so the decay of R is kept to a constant
+//              factor; Y0 itself when n' <= 2b).
 // Training kernels: per-sample forward, per-sample backward, gradient
 // reductions over the batch in a fixed order (deterministic, no atomics),
 // and Adam.  Cross-entropy loss averaged over the batch.
@@ -60,9 +64,10 @@ __device__ void mlp_forward(const float* P, const float* xin, float* pre1, float
     }
 }
 
-// Features of block step k0 (see the file comment).  R_jj are read from the
-// QR storage of Y0 (ld ldr); the previous block from T.
-__global__ void k_learnq_features(const double* __restrict__ T, int64_t ldt, int64_t k0, int wprev,
+// Features of a block step (see the file comment).  R_jj are read from the
+// QR storage of the compressed sketch (ld ldr); the previous block's d_j from
+// dprev[j * dstride] (wprev = 0: first block).
+__global__ void k_learnq_features(const double* __restrict__ dprev, int64_t dstride, int wprev,
                                   const double* __restrict__ R, int64_t ldr, int w, float* __restrict__ f) {
     const int t = threadIdx.x;
     if (t < 8) {
@@ -73,12 +78,11 @@ __global__ void k_learnq_features(const double* __restrict__ T, int64_t ldt, int
     }
     __syncthreads();
     if (t < 8) {
-        if (k0 == 0 || wprev <= 0) {
+        if (wprev <= 0) {
             f[t] = f[8 + t];
         } else {
-            int64_t p0 = k0 - wprev;
             int j = (t * wprev) / 8;
-            double d0 = fabs(T[p0 + p0 * ldt]), dj = fabs(T[(p0 + j) + (p0 + j) * ldt]);
+            double d0 = fabs(dprev[0]), dj = fabs(dprev[(int64_t)j * dstride]);
             float v = (d0 > 0.0 && dj > 0.0) ? (float)log10(dj / d0) : -16.0f;
             f[t] = fmaxf(v, -16.0f);
         }
@@ -91,10 +95,11 @@ __global__ void k_learnq_features(const double* __restrict__ T, int64_t ldt, int
 // every block the network is unsure about).  No model or a non-finite output
 // gives `fallback`.
 __global__ void k_learnq_infer(const float* __restrict__ P, const float* __restrict__ f, int fallback,
-                               float confidence, int* q) {
+                               float confidence, int* q, int* qlog) {
     if (threadIdx.x != 0) return;
     if (P == nullptr) {
         *q = fallback;
+        if (qlog) *qlog = fallback;
         return;
     }
     float pre1[NH], h1[NH], pre2[NH], h2[NH], lg[NO];
@@ -103,6 +108,7 @@ __global__ void k_learnq_infer(const float* __restrict__ P, const float* __restr
     for (int k = 0; k < NO; ++k) finite &= isfinite(lg[k]);
     if (!finite) {
         *q = fallback;
+        if (qlog) *qlog = fallback;
         return;
     }
     float mx = lg[0];
@@ -122,6 +128,7 @@ __global__ void k_learnq_infer(const float* __restrict__ P, const float* __restr
         }
     }
     *q = choice;
+    if (qlog) *qlog = choice;
 }
 
 // per-sample forward + backward of the mean cross-entropy; writes the
@@ -222,15 +229,15 @@ __global__ void k_sum_loss(const float* __restrict__ l, int N, float* out) {
 
 int learnq_nparam() { return NPARAM; }
 
-cudaError_t learnq_features(const double* T, int64_t ldt, int64_t k0, int wprev, const double* R, int64_t ldr, int w,
+cudaError_t learnq_features(const double* dprev, int64_t dstride, int wprev, const double* R, int64_t ldr, int w,
                             float* f, cudaStream_t st) {
-    k_learnq_features<<<1, 32, 0, st>>>(T, ldt, k0, wprev, R, ldr, w, f);
+    k_learnq_features<<<1, 32, 0, st>>>(dprev, dstride, wprev, R, ldr, w, f);
     trace_count(1);
     return cudaGetLastError();
 }
 
-cudaError_t learnq_infer(const float* P, const float* f, int fallback, int* q, cudaStream_t st) {
-    k_learnq_infer<<<1, 32, 0, st>>>(P, f, fallback, kLearnqConfidence, q);
+cudaError_t learnq_infer(const float* P, const float* f, int fallback, int* q, int* qlog, cudaStream_t st) {
+    k_learnq_infer<<<1, 32, 0, st>>>(P, f, fallback, kLearnqConfidence, q, qlog);
     trace_count(1);
     return cudaGetLastError();
 }

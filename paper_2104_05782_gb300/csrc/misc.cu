@@ -78,6 +78,27 @@ __global__ void k_check_finite(const double* __restrict__ X, int64_t ld, int64_t
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_NONFINITE);
 }
 
+// X(i, j) := 0 below the diagonal (i > j) of a rows x cols matrix.
+__global__ void k_zero_below(double* __restrict__ X, int64_t ld, int64_t rows, int64_t cols) {
+    int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e % rows, j = e / rows;
+        if (i > j) X[i + j * ld] = 0.0;
+    }
+}
+
+// X (m x m) := diag(X(0:n, 0:n), I_{m-n}): every entry outside the leading
+// n x n block is set to the identity's.
+__global__ void k_embed_identity(double* __restrict__ X, int64_t ld, int64_t m, int64_t n) {
+    int64_t total = m * m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e % m, j = e / m;
+        if (i >= n || j >= n) X[i + j * ld] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
 unsigned grid_for(int64_t total) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 8192)); }
 
 }  // namespace
@@ -116,6 +137,20 @@ cudaError_t set_diag_block(double* T, int64_t ldt, int64_t k0, int64_t m, int w,
                            cudaStream_t st) {
     if (w <= 0 || m - k0 <= 0) return cudaSuccess;
     k_set_diag_block<<<grid_for((m - k0) * w), 256, 0, st>>>(T, ldt, k0, m, w, D);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t zero_below_diag(double* X, int64_t ld, int64_t rows, int64_t cols, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    k_zero_below<<<grid_for(rows * cols), 256, 0, st>>>(X, ld, rows, cols);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t embed_identity(double* X, int64_t ld, int64_t m, int64_t n, cudaStream_t st) {
+    if (m <= 0 || m == n) return cudaSuccess;
+    k_embed_identity<<<grid_for(m * m), 256, 0, st>>>(X, ld, m, n);
     trace_count(1);
     return cudaGetLastError();
 }

@@ -108,7 +108,8 @@ __device__ __forceinline__ int scale_of(int maxbe) { return maxbe == 0 ? INT_MIN
 
 // row maxima of the exponent: L(r, k) = trans ? X(k, r) : X(r, k)
 __global__ void k_oz_rowexp(const double* __restrict__ X, int64_t ld, int R, int K, bool trans, int* __restrict__ e,
-                            int* status) {
+                            int* status, DevGate gate) {
+    if (gate_closed(gate)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (trans) {  // row r = column r of X: contiguous, one warp per row
         for (int r = blockIdx.x * 8 + warp; r < R; r += gridDim.x * 8) {
@@ -167,7 +168,8 @@ __device__ __forceinline__ void digits_of(double x, int er, uint32_t* dg) {
 // per digit plane); else a 32 x 32 tile is transposed through shared memory.
 // Columns K..ldq-1 of Q are never read (the tensor map ends at K).
 __global__ void k_oz_split(const double* __restrict__ X, int64_t ld, int R, int K, bool trans,
-                           const int* __restrict__ e, uint16_t* __restrict__ Q, int64_t ldq) {
+                           const int* __restrict__ e, uint16_t* __restrict__ Q, int64_t ldq, DevGate gate) {
+    if (gate_closed(gate)) return;
     const size_t slice = (size_t)R * ldq;
     if (trans) {
         const int64_t kq = (K + 3) / 4;
@@ -268,7 +270,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                                                             double alpha, double beta, double* __restrict__ C,
                                                             int64_t ldc, OzJobs jb, double* __restrict__ P,
                                                             int* status, int a_plane, int a_row0, int b_plane,
-                                                            int b_row0, int amode, int bmode, int* jobctr) {
+                                                            int b_row0, int amode, int bmode, int* jobctr,
+                                                            DevGate gate) {
+    if (gate_closed(gate)) return;
     extern __shared__ __align__(1024) uint8_t oz_raw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)oz_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* Abuf = sm;                                   // OZ_AST x 16 KB
@@ -539,7 +543,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
 
 // C = sum_z P[z] (fixed order) + beta C
 __global__ void k_oz_reduce(int M, int N, int S, const double* __restrict__ P, double beta, int bzero,
-                            double* __restrict__ C, int64_t ldc) {
+                            double* __restrict__ C, int64_t ldc, DevGate gate) {
+    if (gate_closed(gate)) return;
     const int64_t total = (int64_t)M * N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
@@ -613,12 +618,12 @@ cudaError_t oz_split(bool trans, const double* X, int64_t ldx, int64_t R, int64_
     if (R <= 0 || K <= 0) return cudaSuccess;
     if (trans) {
         k_oz_rowexp<<<(unsigned)std::min<int64_t>(cdiv(R, 8), 4096), 256, 0, st>>>(X, ldx, (int)R, (int)K, true, e,
-                                                                                      status);
-        k_oz_split<<<oz_grid(R * cdiv(K, 4)), 256, 0, st>>>(X, ldx, (int)R, (int)K, true, e, Q, ldq);
+                                                                                      status, current_gate());
+        k_oz_split<<<oz_grid(R * cdiv(K, 4)), 256, 0, st>>>(X, ldx, (int)R, (int)K, true, e, Q, ldq, current_gate());
     } else {
-        k_oz_rowexp<<<(unsigned)cdiv(R, 32), 256, 0, st>>>(X, ldx, (int)R, (int)K, false, e, status);
+        k_oz_rowexp<<<(unsigned)cdiv(R, 32), 256, 0, st>>>(X, ldx, (int)R, (int)K, false, e, status, current_gate());
         k_oz_split<<<dim3((unsigned)cdiv(R, 32), (unsigned)cdiv(K, 32)), 256, 0, st>>>(X, ldx, (int)R, (int)K, false,
-                                                                                        e, Q, ldq);
+                                                                                        e, Q, ldq, current_gate());
     }
     trace_count(2);
     return cudaGetLastError();
@@ -659,11 +664,12 @@ cudaError_t oz_product(const OzOperand& a, int64_t a_row0, const OzOperand& b, i
     const int bmode = (beta == 0.0) ? 0 : (beta == 1.0 ? 1 : 2);
     k_oz_gemm<<<grid, OZ_THREADS, OZ_SMEM, st>>>(ma, mb, (int)M, (int)N, a.e + a_row0, b.e + b_row0, alpha, beta, C,
                                                    ldc, jb, P, status, (int)a.plane, (int)a_row0, (int)b.plane,
-                                                   (int)b_row0, amode, bmode, jobctr);
+                                                   (int)b_row0, amode, bmode, jobctr, current_gate());
     trace_count(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || splits == 1) return e;
-    k_oz_reduce<<<oz_grid(M * N), 256, 0, st>>>((int)M, (int)N, splits, P, beta, beta == 0.0 ? 1 : 0, C, ldc);
+    k_oz_reduce<<<oz_grid(M * N), 256, 0, st>>>((int)M, (int)N, splits, P, beta, beta == 0.0 ? 1 : 0, C, ldc,
+                                                  current_gate());
     trace_count(1);
     return cudaGetLastError();
 }

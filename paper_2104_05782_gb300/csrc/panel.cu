@@ -62,7 +62,7 @@ template <bool SLAB>
 __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_t ld, int len, int w,
                                                   double* __restrict__ tau, double* __restrict__ part_d,
                                                   double* __restrict__ piv, unsigned* bar, int* status,
-                                                  int chunk, int ldp) {
+                                                  int chunk, int ldp, long long spin_limit) {
     extern __shared__ double smem[];
     constexpr int NW = PNT / 32;
     double* xsb0 = smem;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
     }
     if (r0 <= 0 && 0 < r1)
         for (int c = tid; c < w; c += PNT) piv[c] = PX(0, c);
-    if (!grid_sync(bar, target, status)) return;
+    if (!grid_sync(bar, target, status, spin_limit)) return;
 
     for (int j = 0; j < w; ++j) {
         const int p = j & 1;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(PNT) k_panel_qr(double* __restrict__ P, int64_
         if (r0 <= j + 1 && j + 1 < r1)
             for (int c = j + 1 + tid; c < w; c += PNT)
                 piv[(size_t)(p ^ 1) * w + c] = PX(j + 1 - r0, c);
-        if (!grid_sync(bar, target, status)) return;
+        if (!grid_sync(bar, target, status, spin_limit)) return;
     }
     if (SLAB) {
         __syncthreads();
@@ -357,7 +357,8 @@ cudaError_t panel_qr(double* P, int64_t ld, int64_t len, int w, double* tau, dou
     if (e != cudaSuccess) return e;
     int len_i = (int)len;
     int ldp_i = ldp;
-    void* args[] = {&P, &ld, &len_i, &w, &tau, &part, &piv, &bar, &status, &chunk, &ldp_i};
+    long long spin_limit = wait_limit();
+    void* args[] = {&P, &ld, &len_i, &w, &tau, &part, &piv, &bar, &status, &chunk, &ldp_i, &spin_limit};
     trace_count(1);
     return cudaLaunchCooperativeKernel(fn, dim3(G), dim3(PNT), args, shm, st);
 }

@@ -17,6 +17,7 @@
 //                         U(:,blk) *= Us; T below the block := 0.
 // When at most b columns remain, the trailing block gets the panel QR and the
 // SVD without a sketch (the Matlab listing of Sec. 3.2 takes a full SVD there).
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <new>
@@ -32,9 +33,27 @@
 namespace rutv {
 
 namespace {
+std::atomic<long long> g_wait_limit{kSpinLimit};
+std::atomic<int> g_sweep_cap{30};
+}  // namespace
+
+namespace {
+thread_local DevGate t_gate{nullptr, 0};
+}  // namespace
+
+const DevGate& current_gate() { return t_gate; }
+GateScope::GateScope(const int* flag, int need) : saved_flag_(t_gate.flag), saved_need_(t_gate.need) {
+    t_gate = DevGate{flag, need};
+}
+GateScope::~GateScope() { t_gate = DevGate{saved_flag_, saved_need_}; }
+
+long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+int sweep_cap() { return g_sweep_cap.load(std::memory_order_relaxed); }
+
+namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kMaxSweeps = 30;
+constexpr int kDefaultSweeps = 30;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -65,9 +84,10 @@ struct Workspace {
     size_t oz2_bytes;
     double* tmp2;
     double* part2;
+    int* qlog;        // learned mode: the q chosen at each sketch step (-1: none)
 };
 
-constexpr int kSlots = 36;
+constexpr int kSlots = 37;
 struct Layout {
     size_t off[kSlots];
     size_t total;
@@ -91,6 +111,17 @@ size_t defer_elems(int64_t m, int64_t n, int b) {
     return e;
 }
 
+// Doubles kept by the QR-first phase: per panel of b columns its W
+// ((m - k0) x w) and its triangular factor (w x w).
+size_t qr_defer_elems(int64_t m, int64_t n, int b) {
+    size_t e = 0;
+    for (int64_t k0 = 0; k0 < n; k0 += b) {
+        const int64_t w = std::min<int64_t>(b, n - k0);
+        e += (size_t)(m - k0) * w + (size_t)w * w;
+    }
+    return e;
+}
+
 bool lowp_prec(int prec) {
     return prec == RANDUTV_SKETCH_BF16 || prec == RANDUTV_SKETCH_FP16_SCALED || prec == RANDUTV_EMULATED_SKETCH_BF16;
 }
@@ -109,7 +140,7 @@ int device_sms(int dev) {
     return sms;
 }
 
-Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec) {
+Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec, bool qr_first = false) {
     Layout L{};
     int64_t mx = std::max<int64_t>(std::max(m, n), 1);
     int64_t bb = std::max(b, 1);
@@ -150,10 +181,12 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec) {
         emulated_prec(prec) ? oz_operand_bytes(m, n) : 0,                               // T(:, k0:n) by rows
         emulated_prec(prec) ? oz_operand_bytes(n, m) : 0,                               // T22 by columns
         svd_precond_width((int)wmax) ? sizeof(double) * 5 * (size_t)wmax * wmax : 0,   // preconditioned SVD
-        sizeof(double) * defer_elems(m, n, b),                                          // deferred U / V
+        sizeof(double) * (qr_first ? qr_defer_elems(m, n, b) + defer_elems(n, n, b)
+                                   : defer_elems(m, n, b)),                             // deferred U / V
         emulated_prec(prec) ? 2 * oz_operand_bytes(mx, std::max<int64_t>(wmax, 128)) + 8192 : 0,  // side Ozaki
         sizeof(double) * (size_t)mx * wmax,                                             // side tmp
-        sizeof(double) * part};                                                         // side partials
+        sizeof(double) * part,                                                          // side partials
+        sizeof(int) * (size_t)(n / std::max(b, 1) + 2)};                                 // learned q per step
     size_t o = 0;
     for (int i = 0; i < kSlots; ++i) {
         L.off[i] = o;
@@ -209,6 +242,7 @@ Workspace carve(void* base, const Layout& L) {
     w.oz2_bytes = L.off[34] - L.off[33];
     w.tmp2 = (double*)(p + L.off[34]);
     w.part2 = (double*)(p + L.off[35]);
+    w.qlog = (int*)(p + L.off[36]);
     return w;
 }
 
@@ -281,6 +315,7 @@ struct SideStream {
     cudaEvent_t ready = nullptr, done = nullptr;      // FP32 Jacobi overlapping the left update
     cudaEvent_t panel = nullptr, right = nullptr;     // main -> side: panel factored, right update done
     cudaEvent_t applied = nullptr;                    // side -> main: small SVD applied to T
+    cudaEvent_t svd_done = nullptr;                   // side -> main: small SVD computed (D ready)
 };
 std::mutex g_side_mu;
 std::unordered_map<int, SideStream> g_side;
@@ -298,6 +333,7 @@ cudaError_t side_stream(SideStream** out) {
         if ((e = cudaEventCreateWithFlags(&s.panel, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&s.right, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&s.applied, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&s.svd_done, cudaEventDisableTiming)) != cudaSuccess) return e;
     }
     *out = &s;
     return cudaSuccess;
@@ -326,11 +362,12 @@ struct Ctx {
     int b, q, prec;
     int mode = MODE_FIXED;
     bool have_model = false;
-    int* q_used = nullptr;            // host, one entry per sketch step (learned mode)
     float* tr_feat = nullptr;         // host, 16 per block (trace mode)
     int* tr_label = nullptr;          // host, one per block (trace mode)
     double* tr_cand = nullptr;        // host, 4 x b per block (trace mode), optional
     int64_t tr_max = 0, tr_count = 0;
+    int64_t tr_stride = 1;            // trace mode: record every tr_stride-th sketch step ...
+    int64_t tr_offset = 0;            // ... starting at this one
     uint64_t seed;
     double *U, *T, *V;
     Workspace w;
@@ -346,6 +383,20 @@ struct Ctx {
     };
     std::vector<Step> steps;
     size_t defer_top = 0;
+    // QR-first phase (Sec. 5.1): each panel's W and triangular factor
+    struct QrStep {
+        int64_t k0;
+        int w;
+        size_t wu, tu;
+    };
+    std::vector<QrStep> qr;
+    int64_t ldu = 0, ldv = 0;      // leading dimensions of U and V
+    // tolerance stop and resume
+    double rank_tol = 0.0, t00 = 0.0;
+    int64_t cols_done = 0, rank = 0;
+    int64_t start_step = 0;
+    bool resume = false;
+    std::vector<double> dhost;     // the last block's diagonal, read by the host
     // overlap of the small SVD with the next block step (fixed-q mode)
     bool overlap = false;
     int64_t pending = -1;        // step whose small SVD still has to be applied to T
@@ -518,7 +569,7 @@ cudaError_t svd_block(Ctx& c, const double* R, int64_t ldr, int w, bool started)
     TraceScope tsv("jacobi_svd", 0.0, 8.0 * 3.0 * (double)w * w, c.st);
     if (!started)
         return jacobi_svd(R, ldr, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status,
-                          kMaxSweeps, c.st);
+                          sweep_cap(), c.st);
     SideStream* ss = nullptr;
     CK(side_stream(&ss));
     CK(cudaStreamWaitEvent(c.st, ss->done, 0));
@@ -537,7 +588,7 @@ cudaError_t svd_block(Ctx& c, const double* R, int64_t ldr, int w, bool started)
     CK(triu_copy(R, ldr, w, Ru, c.st));
     CK(gemm(c, "svd_precond", false, false, w, w, w, 1.0, Ru, w, Q, w, 0.0, X, w));
     TraceScope t64("jacobi_fp64", 0.0, 0.0, c.st);
-    return jacobi_svd(X, w, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status, kMaxSweeps,
+    return jacobi_svd(X, w, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status, sweep_cap(),
                       c.st, true, true, Q);
 }
 
@@ -573,9 +624,11 @@ cudaError_t svd_side(Ctx& c, const double* R, int64_t ldr, int w) {
     CK(cudaStreamWaitEvent(ss->st, ss->panel, 0));
     Ctx c2 = side_ctx(c, ss->st);
     TraceScope tsv("jacobi_svd", 0.0, 8.0 * 3.0 * (double)w * w, c2.st);
-    if (!c.w.svdp || !svd_precond_width(w))
-        return jacobi_svd(R, ldr, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status,
-                          kMaxSweeps, c2.st);
+    if (!c.w.svdp || !svd_precond_width(w)) {
+        CK(jacobi_svd(R, ldr, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status,
+                      sweep_cap(), c2.st));
+        return cudaEventRecord(ss->svd_done, c2.st);
+    }
     const size_t w2 = (size_t)w * w;
     double* Q = c.w.svdp;
     double* Q1 = Q + w2;
@@ -595,8 +648,9 @@ cudaError_t svd_side(Ctx& c, const double* R, int64_t ldr, int w) {
     CK(triu_copy(R, ldr, w, Ru, c2.st));
     CK(gemm(c2, "svd_precond", false, false, w, w, w, 1.0, Ru, w, Q, w, 0.0, X, w));
     TraceScope t64("jacobi_fp64", 0.0, 0.0, c2.st);
-    return jacobi_svd(X, w, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status, kMaxSweeps,
-                      c2.st, true, true, Q);
+    CK(jacobi_svd(X, w, w, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status, sweep_cap(),
+                  c2.st, true, true, Q));
+    return cudaEventRecord(ss->svd_done, c2.st);
 }
 
 // Applies the pending step's Us, Vs on the side stream once the main stream
@@ -706,16 +760,44 @@ cudaError_t apply_left(Ctx& c, const double* W, const double* Tf, double* X, int
 // S_i X just writes s_i into the diagonal block and Q_i touches X(k0_i:, k0_i:)
 // only: (n - k0_i)^2 instead of n (n - k0_i) per step, a third less work than
 // updating V at every step.
-cudaError_t accumulate(Ctx& c, double* X, int64_t nx, bool is_v) {
-    CK(set_identity(X, nx, nx, c.st));
+cudaError_t accumulate(Ctx& c, double* X, int64_t nx, int64_t ldx, bool is_v) {
+    CK(set_identity(X, nx, ldx, c.st));
     for (int64_t i = (int64_t)c.steps.size() - 1; i >= 0; --i) {
         const Ctx::Step& r = c.steps[(size_t)i];
-        double* Xb = X + r.k0 + r.k0 * nx;
-        CK(copy_matrix(c.w.defer + (is_v ? r.vs : r.us), r.w, Xb, nx, r.w, r.w, c.st));
+        double* Xb = X + r.k0 + r.k0 * ldx;
+        CK(copy_matrix(c.w.defer + (is_v ? r.vs : r.us), r.w, Xb, ldx, r.w, r.w, c.st));
         if (is_v && !r.sketch) continue;
         const int w = is_v ? c.b : r.w;
-        CK(apply_left(c, c.w.defer + (is_v ? r.wv : r.wu), c.w.defer + (is_v ? r.tv : r.tu), Xb, nx, nx - r.k0,
+        CK(apply_left(c, c.w.defer + (is_v ? r.wv : r.wu), c.w.defer + (is_v ? r.tv : r.tu), Xb, ldx, nx - r.k0,
                       nx - r.k0, w));
+    }
+    return cudaSuccess;
+}
+
+// C (rows x cols) := C (I - W Tf W^T) with W (cols x w, ld cols) and Tf (w x w).
+cudaError_t apply_right_wy(Ctx& c, double* C, int64_t ldc, int64_t rows, int64_t cols, const double* W,
+                           const double* Tf, int w) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    CK(gemm(c, "gemm_accumulate", false, false, rows, w, cols, 1.0, C, ldc, W, cols, 0.0, c.w.X, rows));
+    CK(gemm(c, "gemm_accumulate_tf", false, false, rows, w, w, 1.0, c.w.X, rows, Tf, w, 0.0, c.w.X2, rows));
+    return gemm(c, "gemm_accumulate", false, true, rows, cols, w, -1.0, c.w.X2, rows, W, cols, 1.0, C, ldc);
+}
+
+// Forward accumulation into orthogonal factors that already hold a partial
+// factorization (resume): with the new steps' Q_i = I - W_i Tf_i W_i^T on
+// columns k0_i.. and S_i on the block columns, X := X Q_i S_i for each new
+// step in order (the per-step updates of the paper's loop).
+cudaError_t accumulate_forward(Ctx& c, double* X, int64_t nx, int64_t ldx, bool is_v) {
+    for (const Ctx::Step& r : c.steps) {
+        double* Xc = X + r.k0 * ldx;
+        if (!is_v || r.sketch) {
+            const int w = is_v ? c.b : r.w;
+            CK(apply_right_wy(c, Xc, ldx, nx, nx - r.k0, c.w.defer + (is_v ? r.wv : r.wu),
+                              c.w.defer + (is_v ? r.tv : r.tu), w));
+        }
+        CK(gemm(c, "gemm_accumulate", false, false, nx, r.w, r.w, 1.0, Xc, ldx, c.w.defer + (is_v ? r.vs : r.us),
+                r.w, 0.0, c.w.tmp, nx));
+        CK(copy_matrix(c.w.tmp, nx, Xc, ldx, nx, r.w, c.st));
     }
     return cudaSuccess;
 }
@@ -804,12 +886,45 @@ cudaError_t fp64_iterate(Ctx& c, int64_t k0, double* Y, int iters) {
     return cudaSuccess;
 }
 
-// Features of this block (needs Y0 in c.w.Y): Householder R of a copy of Y0.
-cudaError_t block_features(Ctx& c, int64_t k0, int64_t np) {
-    TraceScope ts("learnq_features", 0.0, 16.0 * (double)np * c.b, c.st);
-    CK(copy_matrix(c.w.Y, np, c.w.Z, np, np, c.b, c.st));
-    CK(panel_qr(c.w.Z, np, np, c.b, c.w.tau, c.w.pscr, c.w.bars, c.w.status, panel_sms(c), c.st));
-    return learnq_features(c.T, c.ldt, k0, k0 > 0 ? c.b : 0, c.w.Z, np, c.b, c.w.feat, c.st);
+// Step index of the Gaussian draws that compress the sketch for the
+// features, far from the sketch steps' own indices.
+constexpr int64_t kFeatureDrawStep = (int64_t)1 << 40;
+
+// Features of block step i (needs Y0 = T22^T G in c.w.Y): the Householder R
+// of E = Omega Y0 (2b x b, two Gaussian draws Omega_1, Omega_2 of b rows each;
+// E = Y0 when n' <= 2b) and the previous block's diagonal, read from
+// dprev[j * dstride].
+cudaError_t block_features(Ctx& c, int64_t i, int64_t np, const double* dprev, int64_t dstride) {
+    const int b = c.b;
+    TraceScope ts("learnq_features", 4.0 * (double)np * b * b, 16.0 * (double)np * b, c.st);
+    const int64_t e = std::min<int64_t>(2 * (int64_t)b, np);
+    double* E = c.w.X2;  // e x b, ld e
+    if (np <= 2 * (int64_t)b) {
+        CK(copy_matrix(c.w.Y, np, E, e, np, b, c.st));
+    } else {
+        for (int h = 0; h < 2; ++h) {
+            CK(gaussian_f64(c.seed, kFeatureDrawStep + 2 * i + h, np, b, c.w.Z, np, c.st));
+            CK(gemm(c, "learnq_features", true, false, b, b, np, 1.0, c.w.Z, np, c.w.Y, np, 0.0, E + h * b, e));
+        }
+    }
+    CK(panel_qr(E, e, e, b, c.w.tau, c.w.pscr, c.w.bars, c.w.status, panel_sms(c), c.st));
+    return learnq_features(dprev, dstride, dprev ? b : 0, E, e, b, c.w.feat, c.st);
+}
+
+// The cached splits of T(:, k0:n) (rows) and T22 (columns), made now, outside
+// any launch gate, so that the host's record of them is always true.
+cudaError_t prefetch_splits(Ctx& c, int64_t k0) {
+    const int64_t mp = c.m - k0, np = c.n - k0;
+    cudaError_t e = cudaSuccess;
+    if (oz_shape(c, np, c.b, mp)) {
+        oz_cols_of(c, k0, &e);
+        CK(e);
+    }
+    if (oz_shape(c, mp, c.b, np)) {
+        oz_rows_of(c, k0, &e);
+        CK(e);
+    }
+    return cudaSuccess;
 }
 
 // Trace mode: diagonal the step would produce with q = 0..3, i.e. the
@@ -833,7 +948,7 @@ cudaError_t trace_candidates(Ctx& c, int64_t k0) {
         CK(sketch_gemm(c, false, k0, c.w.X, np, c.w.Z, mp));
         CK(panel_qr(c.w.Z, mp, mp, b, c.w.tau, c.w.pscr, c.w.bars, c.w.status, c.sms, c.st));
         CK(jacobi_svd(c.w.Z, mp, b, c.w.D, c.w.Us, c.w.Vs, c.w.jscr, c.w.bars + 1, c.w.counters, c.w.status,
-                      kMaxSweeps, c.st));
+                      sweep_cap(), c.st));
         CK(cudaMemcpyAsync(c.w.dq + (size_t)q * b, c.w.D, sizeof(double) * b, cudaMemcpyDeviceToDevice, c.st));
     }
     return cudaSuccess;
@@ -860,9 +975,13 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
             CK(fp64_begin(c, i, k0));
             CK(fp64_iterate(c, k0, c.w.Y, iters));
         }
+    } else if (c.mode == MODE_TRACE && i > 0 && (i % c.tr_stride != c.tr_offset || c.tr_count >= c.tr_max)) {
+        CK(fp64_begin(c, i, k0));  // a step that is not recorded: the q = 2 trajectory itself
+        CK(fp64_iterate(c, k0, c.w.Y, 2));
     } else if (c.mode == MODE_TRACE) {
         CK(fp64_begin(c, i, k0));
-        CK(block_features(c, k0, np));
+        const int64_t p0 = k0 - b;  // the previous diagonal block, already in T (serial mode)
+        CK(block_features(c, i, np, k0 > 0 ? c.T + p0 + p0 * ldt : nullptr, ldt + 1));
         CK(trace_candidates(c, k0));
         if (c.tr_count < c.tr_max) {
             double cand[4 * 512];
@@ -870,14 +989,18 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
                                c.st));
             CK(cudaMemcpyAsync(cand, c.w.dq, sizeof(double) * 4 * b, cudaMemcpyDeviceToHost, c.st));
             CK(cudaStreamSynchronize(c.st));
-            // label: smallest q whose diagonal is within 5% of the q = 2 one
-            // (entries below 1e-13 of the block's largest are rounding noise)
+            // label: smallest q whose diagonal is within 5% of the q = 2 one;
+            // entries below 1e-13 of the largest singular value estimate (the
+            // first block's first entry) are rounding noise and are skipped,
+            // so a block made only of noise is labelled 0
+            if (i == 0) c.t00 = cand[2 * b];
+            const double floor_ = 1e-13 * std::max(c.t00, cand[2 * b]);
             int label = 2;
             for (int q = 0; q < 2; ++q) {
                 double worst = 0.0;
                 for (int j = 0; j < b; ++j) {
                     double ref = cand[2 * b + j];
-                    if (!(ref > 1e-13 * cand[2 * b])) continue;
+                    if (!(ref > floor_)) continue;
                     worst = std::max(worst, std::fabs(cand[q * b + j] / ref - 1.0));
                 }
                 if (worst <= 0.05) {
@@ -890,26 +1013,39 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
                 for (int e = 0; e < 4 * b; ++e) c.tr_cand[(size_t)c.tr_count * 4 * b + e] = cand[e];
             ++c.tr_count;
         }
-    } else {  // MODE_LEARNED
+    } else {  // MODE_LEARNED: q is chosen and applied on the device
         if (lowp) {
             CK(lowp_begin(c, i, T22, ls));
             CK(lowp_finish(c, ls));
         } else {
             CK(fp64_begin(c, i, k0));
         }
-        CK(block_features(c, k0, np));
-        int qh = c.q;
-        CK(learnq_infer(c.have_model ? c.w.qmodel : nullptr, c.w.feat, c.q, c.w.qdev, c.st));
-        CK(cudaMemcpyAsync(&qh, c.w.qdev, sizeof(int), cudaMemcpyDeviceToHost, c.st));
-        CK(cudaStreamSynchronize(c.st));
-        iters = std::min(std::max(qh, 0), 3);
-        if (c.q_used) c.q_used[i] = iters;
-        if (lowp) {
-            CK(lowp_iterate(c, ls, iters));
-            CK(lowp_finish(c, ls));
-        } else {
-            CK(fp64_iterate(c, k0, c.w.Y, iters));
+        // the previous block's diagonal: its SVD's D once that SVD is done
+        // (overlapped on the side stream), or T's diagonal (serial)
+        const double* dprev = nullptr;
+        int64_t dstride = 1;
+        if (k0 > 0 && c.overlap) {
+            SideStream* ss = nullptr;
+            CK(side_stream(&ss));
+            CK(cudaStreamWaitEvent(c.st, ss->svd_done, 0));
+            dprev = c.w.D;
+        } else if (k0 > 0) {
+            dprev = c.T + (k0 - b) * (ldt + 1);
+            dstride = ldt + 1;
         }
+        CK(block_features(c, i, np, dprev, dstride));
+        CK(learnq_infer(c.have_model ? c.w.qmodel : nullptr, c.w.feat, c.q, c.w.qdev, c.w.qlog + i, c.st));
+        if (!lowp) CK(prefetch_splits(c, k0));
+        // every iteration up to q = 3 is queued; the kernels of iteration it
+        // run only when the chosen q (device) is at least it + 1
+        for (int it = 0; it < 3; ++it) {
+            GateScope gate(c.w.qdev, it + 1);
+            if (lowp)
+                CK(lowp_iterate(c, ls, 1));
+            else
+                CK(fp64_iterate(c, k0, c.w.Y, 1));
+        }
+        if (lowp) CK(lowp_finish(c, ls));
     }
     CK(factor_panel(c, c.w.Y, np, np, b));
     CK(apply_right_T(c, k0, b));
@@ -923,38 +1059,113 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
     return panel_and_svd(c, k0, b);
 }
 
-cudaError_t run_factor(Ctx& c, const double* A, int64_t lda, int64_t stop_after) {
-    const int64_t m = c.m, n = c.n;
-    if (A != c.T) CK(copy_matrix(A, lda, c.T, c.ldt, m, n, c.st));
-    CK(check_finite(c.T, c.ldt, m, n, c.w.status, c.st));
-    c.steps.clear();
-    c.defer_top = 0;
-    c.pending = -1;
-    c.applied_pending = false;
-    // the learned mode reads the previous diagonal block for its features, and
-    // the trace mode uses the SVD buffers itself: both stay serial
-    c.overlap = (c.mode == MODE_FIXED);
-    for (int64_t i = 0;; ++i) {
-        if (stop_after >= 0 && i >= stop_after) break;
-        int64_t k0 = i * (int64_t)c.b;
-        int64_t np = n - k0;
-        if (np <= 0) break;
-        if (np <= c.b) {
-            CK(panel_and_svd(c, k0, (int)np));
-            break;
-        }
-        CK(sketch_step(c, i));
+// Tolerance stop (Sec. 1.1: stop once the rank is revealed): the host reads
+// the diagonal D of the block step just queued (on the stream its SVD runs
+// on) and stops after the first block whose smallest entry is at most
+// rank_tol |T_00|.
+cudaError_t tol_check(Ctx& c, int64_t k0, int w, bool* stop) {
+    *stop = false;
+    c.dhost.assign((size_t)w, 0.0);
+    cudaStream_t st = c.st;
+    if (c.overlap) {
+        SideStream* ss = nullptr;
+        CK(side_stream(&ss));
+        st = ss->st;
     }
-    CK(flush_pending(c));
-    CK(wait_applied(c));
-    if (c.V) CK(accumulate(c, c.V, n, true));
-    if (c.U) CK(accumulate(c, c.U, m, false));
+    CK(cudaMemcpyAsync(c.dhost.data(), c.w.D, sizeof(double) * (size_t)w, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (k0 == 0) c.t00 = std::fabs(c.dhost[0]);
+    const double thr = c.rank_tol * c.t00;
+    for (int j = 0; j < w; ++j)
+        if (std::fabs(c.dhost[(size_t)j]) > thr) ++c.rank;
+    *stop = !(std::fabs(c.dhost[(size_t)w - 1]) > thr);
     return cudaSuccess;
 }
 
+cudaError_t run_factor(Ctx& c, const double* A, int64_t lda, int64_t stop_after) {
+    const int64_t m = c.m, n = c.n;
+    if (!c.resume && A != c.T) CK(copy_matrix(A, lda, c.T, c.ldt, m, n, c.st));
+    CK(check_finite(c.T, c.ldt, m, n, c.w.status, c.st));
+    c.steps.clear();
+    c.pending = -1;
+    c.applied_pending = false;
+    // the trace mode uses the SVD buffers itself and stays serial; the learned
+    // mode reads the previous block's D as soon as its SVD is done
+    c.overlap = (c.mode == MODE_FIXED || c.mode == MODE_LEARNED);
+    c.cols_done = std::min<int64_t>(n, c.start_step * (int64_t)c.b);
+    for (int64_t i = c.start_step;; ++i) {
+        if (stop_after >= 0 && i - c.start_step >= stop_after) break;
+        const int64_t k0 = i * (int64_t)c.b;
+        const int64_t np = n - k0;
+        if (np <= 0) break;
+        const int w = (int)std::min<int64_t>(np, c.b);
+        if (np <= c.b)
+            CK(panel_and_svd(c, k0, w));
+        else
+            CK(sketch_step(c, i));
+        c.cols_done = k0 + w;
+        if (c.rank_tol > 0.0) {
+            bool stop = false;
+            CK(tol_check(c, k0, w, &stop));
+            if (stop) break;
+        }
+        if (np <= c.b) break;
+    }
+    CK(flush_pending(c));
+    CK(wait_applied(c));
+    if (c.resume) {
+        if (c.V) CK(accumulate_forward(c, c.V, n, c.ldv, true));
+        if (c.U) CK(accumulate_forward(c, c.U, m, c.ldu, false));
+    } else {
+        if (c.V) CK(accumulate(c, c.V, n, c.ldv, true));
+        if (c.U) CK(accumulate(c, c.U, m, c.ldu, false));
+    }
+    return cudaSuccess;
+}
+
+// randUTV with a QR first, for tall inputs (Sec. 5.1): blocked Householder QR
+// A = Q_A [R; 0] (panels of b columns, each with its compact WY factor and a
+// left update of the columns to its right), T := [R; 0], randUTV of the n x n
+// R in place (its U_R lands in U(0:n, 0:n)), then U := Q_A diag(U_R, I) by
+// applying the panels' reflectors from the left, last panel first.
+cudaError_t run_qr_first(Ctx& c, const double* A, int64_t lda, int64_t stop_after) {
+    const int64_t m = c.m, n = c.n, ldt = c.ldt;
+    if (A != c.T) CK(copy_matrix(A, lda, c.T, ldt, m, n, c.st));
+    CK(check_finite(c.T, ldt, m, n, c.w.status, c.st));
+    c.qr.clear();
+    c.overlap = false;
+    for (int64_t k0 = 0; k0 < n; k0 += c.b) {
+        const int w = (int)std::min<int64_t>(c.b, n - k0);
+        const int64_t mp = m - k0;
+        CK(factor_panel(c, c.T + k0 + k0 * ldt, ldt, mp, w));
+        if (n - k0 - w > 0) CK(apply_left_t(c, c.T + k0 + (k0 + w) * ldt, ldt, mp, n - k0 - w, w));
+        if (c.U) {
+            Ctx::QrStep q{k0, w, 0, 0};
+            CK(defer_put(c, c.w.W, mp, mp, w, &q.wu));
+            CK(defer_put(c, c.w.Tf, w, w, w, &q.tu));
+            c.qr.push_back(q);
+        }
+    }
+    CK(zero_below_diag(c.T, ldt, m, n, c.st));
+    c.m = n;  // randUTV of R = T(0:n, 0:n); rows n..m of T stay zero
+    c.oc = OzCache{};
+    const cudaError_t e = run_factor(c, c.T, ldt, stop_after);
+    c.m = m;
+    c.oc = OzCache{};
+    CK(e);
+    if (c.U) {
+        CK(embed_identity(c.U, c.ldu, m, n, c.st));
+        for (auto it = c.qr.rbegin(); it != c.qr.rend(); ++it)
+            CK(apply_left(c, c.w.defer + it->wu, c.w.defer + it->tu, c.U + it->k0, c.ldu, m - it->k0, m, it->w));
+    }
+    return cudaSuccess;
+}
+
+// A wait that gave up leaves the kernels after it working on partial data,
+// which may then also raise the other flags, so a timeout is reported first.
 randutv_status status_from_bits(int bits) {
-    if (bits & ST_NONFINITE) return RANDUTV_ENONFINITE;
     if (bits & ST_TIMEOUT) return RANDUTV_ETIMEOUT;
+    if (bits & ST_NONFINITE) return RANDUTV_ENONFINITE;
     if (bits & ST_NOCONV) return RANDUTV_ENOCONV;
     return RANDUTV_OK;
 }
@@ -989,6 +1200,11 @@ const char* randutv_status_string(int s) {
     }
 }
 
+void randutv_set_limits(int64_t wait_polls, int max_sweeps) {
+    g_wait_limit.store(wait_polls > 0 ? (long long)wait_polls : kSpinLimit, std::memory_order_relaxed);
+    g_sweep_cap.store(max_sweeps > 0 ? max_sweeps : kDefaultSweeps, std::memory_order_relaxed);
+}
+
 size_t randutv_workspace_size(int64_t m, int64_t n, int b, int prec) {
     if (m < n || n < 0 || b < 1) return 0;
     if (!valid_prec(prec)) return 0;
@@ -1002,6 +1218,15 @@ size_t randutv_workspace_size(int64_t m, int64_t n, int b, int prec) {
 namespace rutv {
 namespace {
 
+// Options of randutv_factor_opt (see the header).
+struct FactorOpts {
+    int64_t start_col = 0;
+    double rank_tol = 0.0;
+    bool qr_first = false;
+    int64_t* cols_done = nullptr;
+    int64_t* rank = nullptr;
+};
+
 struct ModeArgs {
     int mode = MODE_FIXED;
     const float* model = nullptr;  // host parameters (learned mode)
@@ -1011,11 +1236,12 @@ struct ModeArgs {
     double* tr_cand = nullptr;
     int64_t tr_max = 0;
     int64_t* tr_count = nullptr;
+    int64_t tr_stride = 1;
 };
 
 randutv_status factor_impl(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, uint64_t seed, double* U,
                            double* T, double* V, int prec, void* stream, void* workspace, size_t ws_bytes,
-                           int64_t stop_after, int* info, const ModeArgs& ma) {
+                           int64_t stop_after, int* info, const ModeArgs& ma, const FactorOpts& fo = FactorOpts{}) {
     if (!args_ok(m, n, A, lda, b, q, T)) return RANDUTV_EINVAL;
     if (!valid_prec(prec)) return RANDUTV_ENOTIMPL;
     if (A == T && lda != m) return RANDUTV_EINVAL;
@@ -1023,7 +1249,7 @@ randutv_status factor_impl(int64_t m, int64_t n, const double* A, int64_t lda, i
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RANDUTV_ECUDA;
     const int sms = device_sms(dev);
-    Layout L = make_layout(m, n, b, sms, prec);
+    Layout L = make_layout(m, n, b, sms, prec, fo.qr_first);
     void* base = workspace;
     if (base == nullptr) {
         if (cached_workspace(dev, L.total, &base) != cudaSuccess) return RANDUTV_ENOMEM;
@@ -1038,11 +1264,36 @@ randutv_status factor_impl(int64_t m, int64_t n, const double* A, int64_t lda, i
     c.sms = sms;
     c.st = st;
     c.mode = ma.mode;
-    c.q_used = ma.q_used;
     c.tr_feat = ma.tr_feat;
     c.tr_label = ma.tr_label;
     c.tr_cand = ma.tr_cand;
     c.tr_max = ma.tr_max;
+    c.tr_stride = std::max<int64_t>(ma.tr_stride, 1);
+    c.tr_offset = (int64_t)(seed % (uint64_t)c.tr_stride);
+    c.ldu = std::max<int64_t>(m, 1);
+    c.ldv = std::max<int64_t>(n, 1);
+    c.defer_top = 0;
+    c.rank_tol = fo.rank_tol;
+    if (fo.start_col > 0) {  // resume: steps continue at index start_col / b
+        c.resume = true;
+        c.start_step = fo.start_col / b;
+        c.cols_done = fo.start_col;
+        if (fo.rank_tol > 0.0) {  // T_00 and the rank so far from the diagonal already in T
+            c.dhost.assign((size_t)fo.start_col, 0.0);
+            if (cudaMemcpy2DAsync(c.dhost.data(), sizeof(double), T, sizeof(double) * (size_t)(c.ldt + 1),
+                                  sizeof(double), (size_t)fo.start_col, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return RANDUTV_ECUDA;
+            c.t00 = std::fabs(c.dhost[0]);
+            for (double d : c.dhost)
+                if (std::fabs(d) > fo.rank_tol * c.t00) ++c.rank;
+        }
+        if (fo.start_col >= n) {  // nothing left to factor
+            if (fo.cols_done) *fo.cols_done = n;
+            if (fo.rank) *fo.rank = c.rank_tol > 0.0 ? c.rank : n;
+            return RANDUTV_OK;
+        }
+    }
     if (cudaMemsetAsync(c.w.status, 0, sizeof(int), st) != cudaSuccess) return RANDUTV_ECUDA;
     if (lowp_prec(prec)) {  // rows b..npad-1 of the 16-bit B operand stay zero
         size_t bytes = sizeof(uint16_t) * (size_t)tc_gemm_npad(std::min<int64_t>(b, std::max<int64_t>(n, 1))) *
@@ -1055,21 +1306,32 @@ randutv_status factor_impl(int64_t m, int64_t n, const double* A, int64_t lda, i
             return RANDUTV_ECUDA;
         c.have_model = true;
     }
-    if (ma.q_used) {
-        int64_t nb = (n + b - 1) / b;
-        for (int64_t i = 0; i < nb; ++i) ma.q_used[i] = -1;
-    }
+    const int64_t nblocks = (n + b - 1) / b;
+    if (ma.q_used)
+        for (int64_t i = 0; i < nblocks; ++i) ma.q_used[i] = -1;
+    if (ma.mode == MODE_LEARNED && nblocks > 0 &&
+        cudaMemsetAsync(c.w.qlog, 0xFF, sizeof(int) * (size_t)nblocks, st) != cudaSuccess)
+        return RANDUTV_ECUDA;
+    if (fo.cols_done) *fo.cols_done = c.cols_done;
+    if (fo.rank) *fo.rank = c.rank_tol > 0.0 ? c.rank : c.cols_done;
     if (m == 0) return RANDUTV_OK;
     {
         std::lock_guard<std::mutex> lk(enqueue_lock(dev));
-        if (run_factor(c, A, lda, stop_after) != cudaSuccess) return RANDUTV_ECUDA;
+        const cudaError_t e = fo.qr_first ? run_qr_first(c, A, lda, stop_after) : run_factor(c, A, lda, stop_after);
+        if (e != cudaSuccess) return RANDUTV_ECUDA;
     }
+    if (fo.cols_done) *fo.cols_done = c.cols_done;
+    if (fo.rank) *fo.rank = c.rank_tol > 0.0 ? c.rank : c.cols_done;
     if (ma.tr_count) *ma.tr_count = c.tr_count;
     if (info != nullptr) {
         if (cudaMemcpyAsync(info, c.w.status, sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return RANDUTV_ECUDA;
         return RANDUTV_OK;
     }
+    if (ma.mode == MODE_LEARNED && ma.q_used && nblocks > 0 &&
+        cudaMemcpyAsync(ma.q_used, c.w.qlog, sizeof(int) * (size_t)nblocks, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+        return RANDUTV_ECUDA;
     int bits = 0;
     if (cudaMemcpyAsync(&bits, c.w.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return RANDUTV_ECUDA;
@@ -1089,6 +1351,43 @@ randutv_status randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t 
                        ModeArgs{});
 }
 
+void randutv_options_init(randutv_options* opt) {
+    if (!opt) return;
+    *opt = randutv_options{};
+    opt->prec = RANDUTV_FP64;
+    opt->stop_after = -1;
+}
+
+size_t randutv_workspace_size_opt(int64_t m, int64_t n, int b, const randutv_options* opt) {
+    if (m < n || n < 0 || b < 1) return 0;
+    const int prec = opt ? opt->prec : RANDUTV_FP64;
+    if (!valid_prec(prec)) return 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    return make_layout(m, n, b, device_sms(dev), prec, opt && opt->qr_first).total;
+}
+
+randutv_status randutv_factor_opt(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, uint64_t seed,
+                                  double* U, double* T, double* V, randutv_options* opt) {
+    randutv_options o;
+    randutv_options_init(&o);
+    if (opt) o = *opt;
+    if (!(o.rank_tol >= 0.0) || !std::isfinite(o.rank_tol) || o.start_col < 0 || o.start_col > n) return RANDUTV_EINVAL;
+    if (o.start_col > 0 && (b < 1 || (o.start_col % b != 0 && o.start_col != n))) return RANDUTV_EINVAL;
+    if (o.start_col > 0 && o.qr_first) return RANDUTV_EINVAL;
+    FactorOpts fo;
+    fo.start_col = o.start_col;
+    fo.rank_tol = o.rank_tol;
+    fo.qr_first = o.qr_first != 0;
+    fo.cols_done = opt ? &opt->cols_done : nullptr;
+    fo.rank = opt ? &opt->rank : nullptr;
+    // a resumed call does not read A: T stands in for it in the argument checks
+    const double* a = (o.start_col > 0) ? T : A;
+    const int64_t la = (o.start_col > 0) ? std::max<int64_t>(m, 1) : lda;
+    return factor_impl(m, n, a, la, b, q, seed, U, T, V, o.prec, o.stream, o.workspace, o.ws_bytes, o.stop_after,
+                       nullptr, ModeArgs{}, fo);
+}
+
 randutv_status randutv_factor_learnedq_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
                                           const float* model, uint64_t seed, double* U, double* T, double* V,
                                           int* q_used, int prec, void* stream) {
@@ -1104,22 +1403,31 @@ randutv_status randutv_factor_learnedq(int64_t m, int64_t n, const double* A, in
     return randutv_factor_learnedq_ex(m, n, A, lda, b, model, seed, U, T, V, q_used, RANDUTV_FP64, nullptr);
 }
 
-randutv_status randutv_learnq_trace(int64_t m, int64_t n, const double* A, int64_t lda, int b, uint64_t seed,
-                                    double* T, float* features, int* labels, double* candidates, int64_t max_blocks,
-                                    int64_t* nblocks) {
-    if (!features || !labels || max_blocks < 0 || b > 512) return RANDUTV_EINVAL;
+randutv_status randutv_learnq_trace_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b, uint64_t seed,
+                                       double* T, float* features, int* labels, double* candidates,
+                                       int64_t max_blocks, int64_t* nblocks, int prec, int64_t stride) {
+    if (!features || !labels || max_blocks < 0 || b > 512 || stride < 1) return RANDUTV_EINVAL;
+    if (prec != RANDUTV_FP64 && prec != RANDUTV_FP64_EMULATED) return RANDUTV_EINVAL;
     ModeArgs ma;
     ma.mode = MODE_TRACE;
     ma.tr_feat = features;
     ma.tr_label = labels;
     ma.tr_cand = candidates;
     ma.tr_max = max_blocks;
+    ma.tr_stride = stride;
     int64_t cnt = 0;
     ma.tr_count = &cnt;
-    randutv_status r = factor_impl(m, n, A, lda, b, 2, seed, nullptr, T, nullptr, RANDUTV_FP64, nullptr, nullptr, 0,
-                                   -1, nullptr, ma);
+    randutv_status r =
+        factor_impl(m, n, A, lda, b, 2, seed, nullptr, T, nullptr, prec, nullptr, nullptr, 0, -1, nullptr, ma);
     if (nblocks) *nblocks = cnt;
     return r;
+}
+
+randutv_status randutv_learnq_trace(int64_t m, int64_t n, const double* A, int64_t lda, int b, uint64_t seed,
+                                    double* T, float* features, int* labels, double* candidates, int64_t max_blocks,
+                                    int64_t* nblocks) {
+    return randutv_learnq_trace_ex(m, n, A, lda, b, seed, T, features, labels, candidates, max_blocks, nblocks,
+                                   RANDUTV_FP64, 1);
 }
 
 int randutv_learnq_model_floats(void) { return learnq_nparam(); }

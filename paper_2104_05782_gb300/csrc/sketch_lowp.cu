@@ -99,7 +99,8 @@ __global__ void k_pack16(const T* __restrict__ X, int64_t ldx, int L, int b, uin
 
 // X(r, c) = sum_z P[z](r, c) for r < L, c < b (fixed order), column-major ld L.
 __global__ void k_reduce_splits(const float* __restrict__ P, int64_t stride, int splits, int L, int b, int64_t ldp,
-                                float* __restrict__ X) {
+                                float* __restrict__ X, DevGate gate) {
+    if (gate_closed(gate)) return;
     int64_t total = (int64_t)L * b;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t r = e % L, c = e / L;
@@ -117,7 +118,8 @@ __global__ void k_f32_to_f64(const float* __restrict__ X, int64_t total, double*
 // Partial Gram matrices: block g sums rows [g*chunk, (g+1)*chunk) of X^T X.
 // 8 x 8 register micro-tiles over (p, q), rows staged through shared memory.
 __global__ void __launch_bounds__(256) k_gram32(const float* __restrict__ X, int L, int b, int chunk,
-                                                float* __restrict__ Gp) {
+                                                float* __restrict__ Gp, DevGate gate) {
+    if (gate_closed(gate)) return;
     extern __shared__ float xs[];  // 32 rows x b
     const int r0 = blockIdx.x * chunk, r1 = min(L, r0 + chunk);
     const int nt = (b / 8) * (b / 8);
@@ -160,28 +162,45 @@ __global__ void __launch_bounds__(256) k_gram32(const float* __restrict__ X, int
     }
 }
 
-// One block: G = sum of partials (+ shift) and its Cholesky factor G = R^T R
-// (upper R), written column-major b x b to R.  A non-positive pivot
-// (breakdown: the columns were numerically dependent) is replaced by the
-// shift floor; the next pass repairs the basis.  G lives in shared memory
-// when it fits (b <= 128), else in the global scratch Gg.
-__global__ void __launch_bounds__(256) k_chol32(const float* __restrict__ Gp, int nparts, int b, int L, int shift,
-                                                float* __restrict__ Gg, float* __restrict__ R, int use_smem) {
-    extern __shared__ float csm[];
-    __shared__ float s_tr, s_piv;
-    float* G = use_smem ? csm : Gg;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < b * b; e += nt) {
-        const int i = e % b, j = e / b;
-        float s = 0.0f;
-        if (i <= j)
-            for (int g = 0; g < nparts; ++g) s += Gp[(size_t)g * b * b + e];
-        G[e] = s;
-    }
+// G (b x b, upper triangle) = sum of the nparts partial Gram matrices, in a
+// fixed order, spread over many blocks.
+__global__ void k_gram_sum(const float* __restrict__ Gp, int nparts, int b, float* __restrict__ G, DevGate gate) {
+    if (gate_closed(gate)) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= b * b) return;
+    const int i = e % b, j = e / b;
+    float s = 0.0f;
+    if (i <= j)
+        for (int g = 0; g < nparts; ++g) s += Gp[(size_t)g * b * b + e];
+    G[e] = s;
+}
+
+// Packed upper triangle: entry (p, c), p <= c, at c (c + 1) / 2 + p.
+__device__ __forceinline__ int tri(int p, int c) { return c * (c + 1) / 2 + p; }
+constexpr int CHOL_THREADS = 1024;
+
+// One block: Cholesky G (+ shift) = R^T R of the upper triangle of G, with
+// the triangle packed in shared memory (b (b + 1) / 2 floats; 132 KB at
+// b = 256).  Right-looking: step j takes the pivot, then every warp updates
+// whole columns c > j of the trailing triangle (lanes over its rows), reading
+// row j unscaled and multiplying by 1 / pivot on the fly; row j itself is
+// scaled during the next step, so each step needs two barriers.  A
+// non-positive pivot (breakdown: numerically dependent columns) is replaced
+// by the shift floor; the next pass repairs the basis.  R is written
+// column-major b x b.
+__global__ void __launch_bounds__(CHOL_THREADS) k_chol32(const float* __restrict__ G, int b, int L, int shift,
+                                                         float* __restrict__ R, DevGate gate) {
+    if (gate_closed(gate)) return;
+    extern __shared__ float P[];
+    __shared__ float s_tr, s_inv;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NWARP = CHOL_THREADS / 32;
+    for (int c = warp; c < b; c += NWARP)
+        for (int p = lane; p <= c; p += 32) P[tri(p, c)] = G[p + (size_t)c * b];
     __syncthreads();
     if (tid == 0) {
         float tr = 0.0f;
-        for (int i = 0; i < b; ++i) tr += G[i + (size_t)i * b];
+        for (int i = 0; i < b; ++i) tr += P[tri(i, i)];
         s_tr = tr;
     }
     __syncthreads();
@@ -189,52 +208,61 @@ __global__ void __launch_bounds__(256) k_chol32(const float* __restrict__ Gp, in
     const float sh = shift ? 11.0f * ((float)L * b + (float)b * (b + 1)) * u * s_tr : 0.0f;
     const float floor_ = fmaxf(sh, 1e-30f + u * s_tr);
     if (shift)
-        for (int i = tid; i < b; i += nt) G[i + (size_t)i * b] += sh;
+        for (int i = tid; i < b; i += CHOL_THREADS) P[tri(i, i)] += sh;
     __syncthreads();
-    // right-looking Cholesky on the upper triangle: row j of R overwrites row j of G
+    float inv_prev = 1.0f;
     for (int j = 0; j < b; ++j) {
+        // row j - 1 scaled by its pivot's inverse (its last reader was step j - 1)
+        if (j > 0)
+            for (int c = j + tid; c < b; c += CHOL_THREADS) P[tri(j - 1, c)] *= inv_prev;
         if (tid == 0) {
-            float d = G[j + (size_t)j * b];
+            float d = P[tri(j, j)];
             if (!(d > 0.0f)) d = floor_;
-            s_piv = sqrtf(d);
+            const float piv = sqrtf(d);
+            P[tri(j, j)] = piv;
+            s_inv = 1.0f / piv;
         }
         __syncthreads();
-        const float piv = s_piv, inv = 1.0f / piv;
-        // trailing update, one column per thread (row j scaled on the fly)
-        for (int c = j + 1 + tid; c < b; c += nt) {
-            float* gc = G + (size_t)c * b;
-            const float rc = gc[j] * inv;
-            for (int p = j + 1; p <= c; ++p) gc[p] -= (G[j + (size_t)p * b] * inv) * rc;
+        const float inv = s_inv;
+        for (int c = j + 1 + warp; c < b; c += NWARP) {
+            const float rc = P[tri(j, c)] * inv;
+            for (int p = j + 1 + lane; p <= c; p += 32) P[tri(p, c)] -= (P[tri(j, p)] * inv) * rc;
         }
-        __syncthreads();
-        for (int c = j + 1 + tid; c < b; c += nt) G[j + (size_t)c * b] *= inv;
-        if (tid == 0) G[j + (size_t)j * b] = piv;
+        inv_prev = inv;
         __syncthreads();
     }
-    for (int e = tid; e < b * b; e += nt) {
-        const int i = e % b, j = e / b;
-        R[e] = (i <= j) ? G[e] : 0.0f;
+    // (row b - 1 holds only its pivot, so nothing is left to scale)
+    for (int e = tid; e < b * b; e += CHOL_THREADS) {
+        const int i = e % b, c = e / b;
+        R[e] = (i <= c) ? P[tri(i, c)] : 0.0f;
     }
 }
 
-// X := X R^-1 (R upper b x b) by forward substitution, one row per thread;
-// optionally also writes the 16-bit K-major operand Xb[j*ldb + r].
+// X := X R^-1 (R upper b x b) by forward substitution, one row per thread,
+// with R packed in shared memory and four partial sums per entry (a shorter
+// dependent chain); optionally also writes the 16-bit K-major operand
+// Xb[j*ldb + r].
 __global__ void __launch_bounds__(128) k_trsm32(float* __restrict__ X, int L, int b, const float* __restrict__ R,
-                                                uint16_t* __restrict__ Xb, int64_t ldb, bool f16, int use_smem) {
+                                                uint16_t* __restrict__ Xb, int64_t ldb, bool f16, DevGate gate) {
+    if (gate_closed(gate)) return;
     extern __shared__ float rs[];
-    const float* Rr = R;
-    if (use_smem) {
-        for (int e = threadIdx.x; e < b * b; e += blockDim.x) rs[e] = R[e];
-        __syncthreads();
-        Rr = rs;
-    }
+    for (int c = threadIdx.x; c < b; c += blockDim.x)
+        for (int p = 0; p <= c; ++p) rs[tri(p, c)] = R[p + (size_t)c * b];
+    __syncthreads();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= L) return;
     for (int j = 0; j < b; ++j) {
-        float s = X[r + (int64_t)j * L];
-        const float* rc = Rr + (size_t)j * b;
-        for (int k = 0; k < j; ++k) s = fmaf(-X[r + (int64_t)k * L], rc[k], s);
-        s /= rc[j];
+        const float* rc = rs + tri(0, j);
+        float s0 = X[r + (int64_t)j * L], s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+        int k = 0;
+        for (; k + 3 < j; k += 4) {
+            s0 = fmaf(-X[r + (int64_t)k * L], rc[k], s0);
+            s1 = fmaf(-X[r + (int64_t)(k + 1) * L], rc[k + 1], s1);
+            s2 = fmaf(-X[r + (int64_t)(k + 2) * L], rc[k + 2], s2);
+            s3 = fmaf(-X[r + (int64_t)(k + 3) * L], rc[k + 3], s3);
+        }
+        for (; k < j; ++k) s0 = fmaf(-X[r + (int64_t)k * L], rc[k], s0);
+        const float s = ((s0 + s1) + (s2 + s3)) / rc[j];
         X[r + (int64_t)j * L] = s;
         if (Xb) Xb[(int64_t)j * ldb + r] = to16(s, f16);
     }
@@ -271,7 +299,7 @@ cudaError_t pack16_f64(const double* X, int64_t ldx, int64_t L, int b, uint16_t*
 cudaError_t reduce_splits(const float* P, int64_t stride, int splits, int64_t L, int b, int64_t ldp, float* X,
                           cudaStream_t st) {
     if (L <= 0 || b <= 0) return cudaSuccess;
-    k_reduce_splits<<<grid_for(L * b), 256, 0, st>>>(P, stride, splits, (int)L, b, ldp, X);
+    k_reduce_splits<<<grid_for(L * b), 256, 0, st>>>(P, stride, splits, (int)L, b, ldp, X, current_gate());
     trace_count(1);
     return cudaGetLastError();
 }
@@ -286,45 +314,48 @@ cudaError_t f32_to_f64(const float* X, int64_t total, double* Y, cudaStream_t st
 size_t cholqr_scratch_floats(int b, int sms) { return (size_t)(sms + 1) * b * b + 2 * (size_t)b * b; }
 
 // Shifted CholeskyQR, `passes` passes, on X (L x b FP32, column-major ld L);
-// the last pass also writes the 16-bit operand Xb (ld ldb).
+// the last pass also writes the 16-bit operand Xb (ld ldb).  b <= 256.
 cudaError_t cholqr32(float* X, int64_t L, int b, int passes, uint16_t* Xb, int64_t ldb, bool f16, float* scratch,
                      int sms, cudaStream_t st) {
     if (L <= 0 || b <= 0) return cudaSuccess;
-    if (b % 8) return cudaErrorInvalidValue;
-    // few partial Gram matrices keep the single-block reduction short
-    int parts = (int)std::min<int64_t>(std::min(sms, 48), cdiv(L, 256));
+    if (b % 8 || b > 256) return cudaErrorInvalidValue;
+    // partial Gram matrices over up to one block per SM, summed by many blocks
+    int parts = (int)std::min<int64_t>(sms, cdiv(L, 128));
     parts = std::max(parts, 1);
     int chunk = (int)cdiv(L, parts);
     parts = (int)cdiv(L, chunk);
     float* Gp = scratch;
     float* G = scratch + (size_t)sms * b * b;
     float* R = G + (size_t)b * b;
-    const int small = (b <= 128) ? 1 : 0;
-    const size_t shm_chol = small ? sizeof(float) * (size_t)b * b : 0;
-    const size_t shm_trsm = small ? sizeof(float) * (size_t)b * b : 0;
+    const size_t shm_tri = sizeof(float) * (size_t)b * (b + 1) / 2;
     const size_t shm_gram = sizeof(float) * 32 * (size_t)b;
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_gram32, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-        cudaFuncSetAttribute(k_chol32, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4);
-        cudaFuncSetAttribute(k_trsm32, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4);
+        cudaError_t e = cudaFuncSetAttribute(k_gram32, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_chol32, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 257 / 2 * 4);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_trsm32, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 257 / 2 * 4);
+        if (e != cudaSuccess) return e;
         configured = true;
     }
+    const DevGate gate = current_gate();
     for (int p = 0; p < passes; ++p) {
         {
             TraceScope ts("cholqr_gram", 2.0 * (double)L * b * b, 4.0 * (double)L * b, st);
-            k_gram32<<<parts, 256, shm_gram, st>>>(X, (int)L, b, chunk, Gp);
+            k_gram32<<<parts, 256, shm_gram, st>>>(X, (int)L, b, chunk, Gp, gate);
+            k_gram_sum<<<(unsigned)cdiv((int64_t)b * b, 256), 256, 0, st>>>(Gp, parts, b, G, gate);
         }
         {
-            TraceScope ts("cholqr_chol", (double)b * b * b / 3.0, 4.0 * (double)parts * b * b, st);
-            k_chol32<<<1, 256, shm_chol, st>>>(Gp, parts, b, (int)L, p == 0 ? 1 : 0, G, R, small);
+            TraceScope ts("cholqr_chol", (double)b * b * b / 3.0, 8.0 * (double)b * b, st);
+            k_chol32<<<1, CHOL_THREADS, shm_tri, st>>>(G, b, (int)L, p == 0 ? 1 : 0, R, gate);
         }
         {
             TraceScope ts("cholqr_trsm", (double)L * b * b, 8.0 * (double)L * b, st);
-            k_trsm32<<<(unsigned)cdiv(L, 128), 128, shm_trsm, st>>>(X, (int)L, b, R, p == passes - 1 ? Xb : nullptr,
-                                                                      ldb, f16, small);
+            k_trsm32<<<(unsigned)cdiv(L, 128), 128, shm_tri, st>>>(X, (int)L, b, R, p == passes - 1 ? Xb : nullptr,
+                                                                     ldb, f16, gate);
         }
-        trace_count(3);
+        trace_count(4);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(NT) k_jacobi(const double* __restrict__ R, int
                                                double* __restrict__ D, double* __restrict__ Us,
                                                double* __restrict__ Vs, unsigned* bar, int* rot, int* status,
                                                int max_sweeps, double tol, int dense,
-                                               const double* __restrict__ V0) {
+                                               const double* __restrict__ V0, long long spin_limit) {
     __shared__ double red[3 * (NT / 32)];
     __shared__ int s_flag;
     const int tid = threadIdx.x, G = gridDim.x, cta = blockIdx.x;
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(NT) k_jacobi(const double* __restrict__ R, int
             V[r + (size_t)c * w] = V0 ? V0[r + (size_t)c * w] : ((r == c) ? 1.0 : 0.0);
         }
     if (cta == 0 && tid < 3) rot[tid] = 0;
-    if (!grid_sync(bar, target, status)) return;
+    if (!grid_sync(bar, target, status, spin_limit)) return;
 
     bool converged = (w <= 1);
     int sweep = 0;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(NT) k_jacobi(const double* __restrict__ R, int
                     if (tid == 0) atomicAdd(rot + (sweep % 3), 1);
                 }
             }
-            if (!grid_sync(bar, target, status)) return;
+            if (!grid_sync(bar, target, status, spin_limit)) return;
         }
         if (tid == 0) s_flag = __ldcg(rot + (sweep % 3));
         __syncthreads();
@@ -649,10 +649,11 @@ cudaError_t jacobi_svd(const double* R, int64_t ldr, int w, double* D, double* U
     cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     size_t shm = sizeof(double) * (size_t)w;
+    long long spin_limit = wait_limit();
     void* args[] = {(void*)&R,      (void*)&ldr,        (void*)&w,   (void*)&n2,  (void*)&A,
                     (void*)&V,      (void*)&D,          (void*)&Us,  (void*)&Vs,  (void*)&bar,
                     (void*)&counters, (void*)&status,   (void*)&max_sweeps, (void*)&tol, (void*)&dn,
-                    (void*)&V0};
+                    (void*)&V0,     (void*)&spin_limit};
     trace_count(1);
     if (w <= 128)
         return cudaLaunchCooperativeKernel((const void*)k_jacobi<128>, dim3(G), dim3(128), args, shm, st);

@@ -100,7 +100,8 @@ template <int N, int STAGES>
 __global__ void __launch_bounds__(NTHR, 1) k_tc_gemm(const __grid_constant__ CUtensorMap mapA,
                                                       const __grid_constant__ CUtensorMap mapB, int M, int K,
                                                       int kblocks_per_split, uint32_t idesc, float* __restrict__ C,
-                                                      int64_t ldc, int64_t split_stride, int* status) {
+                                                      int64_t ldc, int64_t split_stride, int* status, DevGate gate) {
+    if (gate_closed(gate)) return;
     using L = SmemLayout<N, STAGES>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -277,7 +278,8 @@ cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int K
         configured = true;
     }
     dim3 grid((unsigned)cdiv(M, TM), (unsigned)splits);
-    k_tc_gemm<N, STAGES><<<grid, NTHR, L::TOTAL, st>>>(ma, mb, M, K, kbs, idesc, C, ldc, split_stride, status);
+    k_tc_gemm<N, STAGES><<<grid, NTHR, L::TOTAL, st>>>(ma, mb, M, K, kbs, idesc, C, ldc, split_stride, status,
+                                                       current_gate());
     trace_count(1);
     return cudaGetLastError();
 }

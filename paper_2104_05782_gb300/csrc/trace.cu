@@ -7,6 +7,8 @@
 #include <vector>
 
 #include "../../include/randutv.h"
+#include "common.cuh"
+#include "internal.h"
 #include "trace.h"
 
 namespace rutv {
@@ -45,7 +47,11 @@ TraceScope::TraceScope(const char* cls, double flops, double bytes, cudaStream_t
     : cls_(cls), flops_(flops), bytes_(bytes), st_(st), slot_(-1), start_(g_launches.load()) {
     if (!g_enabled.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> lk(g_mu);
-    Record r{cls, flops, bytes, 0, get_event(), get_event()};
+    // launches under a device gate may not run: their class is marked and
+    // their algorithmic work is not counted
+    const bool gated = current_gate().flag != nullptr;
+    Record r{gated ? std::string(cls) + "_gated" : std::string(cls), gated ? 0.0 : flops, gated ? 0.0 : bytes, 0,
+             get_event(), get_event()};
     cudaEventRecord(r.e0, st);
     g_records.push_back(r);
     slot_ = (int)g_records.size() - 1;

@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import numpy as np
 
-SPECTRA = ("geometric10", "gap", "algebraic", "geometric8", "normal")
+SPECTRA = ("geometric10", "gap", "algebraic", "geometric8", "normal", "exp32", "exp128")
 
 
 def spectrum(kind: str, n: int) -> np.ndarray:
@@ -21,6 +21,9 @@ def spectrum(kind: str, n: int) -> np.ndarray:
     gap:         sigma_i = 1 for i <= n/10, then a gap to 1e-3 and geometric
                  decay to 1e-12 over the remaining indices
     algebraic:   sigma_i = 1 / i
+    exp32, exp128: sigma_i = max(10^(-(i-1)/r), 1e-15), r = 32 or 128: a fixed
+                 decay per index (four or one decade per 128 indices) down to a
+                 floor near FP64 rounding, i.e. a numerically low-rank matrix
     """
     i = np.arange(n, dtype=np.float64)
     if n == 0:
@@ -31,6 +34,9 @@ def spectrum(kind: str, n: int) -> np.ndarray:
         return 10.0 ** (-8.0 * i / max(n - 1, 1))
     if kind == "algebraic":
         return 1.0 / (i + 1.0)
+    if kind in ("exp32", "exp128"):
+        r = 32.0 if kind == "exp32" else 128.0
+        return np.maximum(10.0 ** (-i / r), 1e-15)
     if kind == "gap":
         k = n // 10
         s = np.empty(n)
@@ -110,3 +116,16 @@ def test_matrix_device(m: int, n: int, kind: str, seed_u: int, seed_v: int, devi
     At = _hartley_mix(X.t().contiguous(), gen)   # Q_V (Q_U M0)^T = A^T  (n x m, row-major)
     del X
     return At.t(), s
+
+
+def graded(A: np.ndarray, span: float = 8.0, seed: int = 0) -> np.ndarray:
+    """D_r A D_c with diagonal scalings whose entries run geometrically over
+    [10^-span, 10^span] in a seeded random order, rows and columns drawn
+    independently.  Rows and columns of the result then differ in scale by up
+    to 10^(2 span), the case where scaling each row (or column) of a product
+    operand by its largest entry truncates the small entries most."""
+    m, n = A.shape
+    g = np.random.default_rng(seed)
+    dr = 10.0 ** g.permutation(np.linspace(-span, span, m)) if m > 1 else np.ones(m)
+    dc = 10.0 ** g.permutation(np.linspace(-span, span, n)) if n > 1 else np.ones(n)
+    return np.asfortranarray(dr[:, None] * np.asarray(A, dtype=np.float64) * dc[None, :])

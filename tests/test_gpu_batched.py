@@ -157,3 +157,60 @@ def test_batched_autotune_table(rutv):
     # the table drives a run
     r2, status, _, T2, _ = run_batch(rutv, mats, 0, 1, table=table, want_uv=False)
     assert r2 == 0
+
+
+def _check_against_oracle(mats, b_of, q, U, T, V, seeds):
+    for k, A in enumerate(mats):
+        Uo, To, Vo, rc = oracle.randutv(A, b_of(k), q, seeds[k])
+        assert rc == 0
+        nrm = np.linalg.norm(A)
+        m, n = A.shape
+        assert np.abs(T[k] - To).max() <= 1e-10 * nrm, (k, A.shape)
+        assert np.abs(U[k] @ T[k] - Uo @ To).max() <= 1e-10 * nrm, (k, A.shape)
+        assert np.abs(T[k] @ V[k].T - To @ Vo.T).max() <= 1e-10 * nrm, (k, A.shape)
+        assert np.linalg.norm(A - U[k] @ T[k] @ V[k].T) / nrm <= utv_bound(n)
+        assert np.linalg.norm(U[k].T @ U[k] - np.eye(m)) <= utv_bound(m)
+        assert np.linalg.norm(V[k].T @ V[k] - np.eye(n)) <= utv_bound(n)
+        assert np.array_equal(np.tril(T[k], -1), np.zeros_like(T[k]))
+
+
+def test_batched_b64_large_and_tall_match_oracle(rutv):
+    """b = 64 (the block size the autotuner picks from n = 256 up) on the
+    largest square size of the workload (512), a ragged 300, and tall
+    m = 2n matrices up to 1024 x 512, each against the oracle."""
+    shapes = [(300, 300), (512, 512), (600, 300), (1024, 512), (520, 260), (384, 192)]
+    mats = make_batch(shapes, kind="normal")
+    seeds = [11 + k for k in range(len(mats))]
+    r, status, U, T, V = run_batch(rutv, mats, 64, 2, seeds=seeds)
+    assert r == rutv.RANDUTV_OK and all(s == 0 for s in status)
+    _check_against_oracle(mats, lambda k: 64, 2, U, T, V, seeds)
+
+
+def test_batched_autotuned_workload_slice_matches_oracle(rutv):
+    """The autotuner's table, run on a 32-matrix slice of the 4096-matrix
+    workload's shapes (n log-uniform in [32, 512], 25% with m = 2n), with the
+    block size the table picks for each matrix, against the oracle."""
+    import bench
+
+    ms, ns = bench.batched_shapes(4096)
+    shapes = list(zip(ms, ns))[:32]
+    mats = make_batch(shapes, kind="normal")
+    seeds = list(range(100, 100 + len(mats)))
+    A = [dev(M) for M in mats]
+    T0 = [rutv.colmajor_empty(*M.shape) for M in mats]
+    r, table = rutv.randutv_batched_autotune([M.shape[0] for M in mats], [M.shape[1] for M in mats], A,
+                                             [M.shape[0] for M in mats], None, T0, None, seeds, 2)
+    assert r == 0
+    rows = [tuple(map(int, line.split())) for line in table.strip().splitlines()]
+    assert rows and all(row[3] in (16, 32, 64) for row in rows)
+
+    def b_of(k):
+        m, n = mats[k].shape
+        tall = 1 if m > n else 0
+        hits = [row[3] for row in rows if row[0] <= n <= row[1] and row[2] in (tall, -1)]
+        assert hits, (m, n, table)
+        return hits[0]
+
+    r, status, U, T, V = run_batch(rutv, mats, 0, 2, seeds=seeds, table=table)
+    assert r == rutv.RANDUTV_OK and all(s == 0 for s in status)
+    _check_against_oracle(mats, b_of, 2, U, T, V, seeds)

@@ -92,9 +92,8 @@ def test_learned_path_with_forcing_model_equals_fixed_q(rutv, q):
     assert qu[:-1] == [q] * (len(qu) - 1) and qu[-1] == -1
     Uf, Tf, Vf = rutv.factor(dev(A), b, q, 3)
     torch.cuda.synchronize()
-    # the fixed-q path applies each block's small SVD after the next step's
-    # right update (the two commute); the learned path applies it at once:
-    # the same factorization up to rounding
+    # a forced choice runs the same steps as the fixed-q path (the skipped
+    # iterations' kernels return at once): the same factorization up to rounding
     nrm = np.linalg.norm(A)
     assert np.abs(host(T) - host(Tf)).max() <= 1e-10 * nrm
     assert np.abs(host(U) @ host(T) - host(Uf) @ host(Tf)).max() <= 1e-10 * nrm
@@ -124,11 +123,12 @@ def test_trace_labels_follow_definition(rutv):
     _, Tf, _ = rutv.factor(dev(A), b, 2, 4, want_uv=False)
     torch.cuda.synchronize()
     assert np.abs(Tt - host(Tf)).max() <= 1e-10 * np.linalg.norm(A)  # same up to rounding
+    floor = 1e-13 * cand[0, 2, 0]   # rounding noise: relative to the largest singular value estimate
     for i in range(len(y)):
         d2 = np.diag(Tt)[i * b:(i + 1) * b]
         assert np.abs(cand[i, 2] - d2).max() <= 1e-10 * d2[0]
-        ok = [np.abs(cand[i, q][cand[i, 2] > 1e-13 * cand[i, 2, 0]] /
-                     cand[i, 2][cand[i, 2] > 1e-13 * cand[i, 2, 0]] - 1).max() <= 0.05 for q in (0, 1)]
+        keep = cand[i, 2] > max(floor, 1e-13 * cand[i, 2, 0])
+        ok = [(not keep.any()) or np.abs(cand[i, q][keep] / cand[i, 2][keep] - 1).max() <= 0.05 for q in (0, 1)]
         want = 0 if ok[0] else (1 if ok[1] else 2)
         assert y[i] == want
     # interlacing: no candidate exceeds the true singular values of the trailing matrix
@@ -136,37 +136,67 @@ def test_trace_labels_follow_definition(rutv):
     assert np.all(cand[0] <= s[0] * (1 + 1e-12))
 
 
+def test_trace_sampling_and_emulated_products(rutv):
+    """The strided, emulated trace records step 0 and every stride-th step
+    (offset seed % stride) and labels them as the full FP64 trace does (a
+    label whose worst ratio sits at the 5% threshold may flip with rounding,
+    so one disagreement is allowed)."""
+    m = n = 1024
+    b, seed, stride = 64, 5, 3
+    A = synthetic.test_matrix(m, n, "geometric10", 9, 10)
+    T = rutv.colmajor_empty(m, n)
+    r, F, y, _ = rutv.randutv_learnq_trace(m, n, dev(A), m, b, seed, T)
+    assert r == 0
+    T2 = rutv.colmajor_empty(m, n)
+    r, F2, y2, _ = rutv.randutv_learnq_trace(m, n, dev(A), m, b, seed, T2, prec=rutv.RANDUTV_FP64_EMULATED,
+                                             stride=stride)
+    assert r == 0
+    steps = [i for i in range(n // b - 1) if i == 0 or i % stride == seed % stride]
+    assert len(y2) == len(steps)
+    assert int(np.sum(y2 != y[steps])) <= 1
+    assert np.abs(F2 - F[steps]).max() <= 1e-3
+    assert np.abs(host(T2) - host(T)).max() <= 1e-10 * np.linalg.norm(A)
+
+
+HELD_OUT = ["gap", "geometric10", "algebraic", "normal", "exp32", "exp128"]
+
+
 def test_trained_network_gain_over_q2(rutv):
-    """Held-out matrices (seeds 10^6 + k): reports the power iterations and time
-    the trained network saves against q = 2 and checks that T_ii / sigma_i stays
-    within 5% of the q = 2 result (or closer to 1) on at least 98% of indices."""
+    """Held-out matrices (seeds 10^6 + k), one of each spectrum of the training
+    mix: the trained network must use strictly fewer power iterations and less
+    time than fixed q = 2 over the set, and every T_ii / sigma_i above the
+    noise floor must stay within 5% of the q = 2 result or closer to 1."""
     model = rutv.load_qnet()
     if model is None:
         pytest.skip("no trained network shipped (run python -m paper_2104_05782_gb300.learnq_train)")
-    kinds = ["geometric10", "algebraic", "gap", "geometric8"]
     n, b = 2048, 128
     t_l = t_2 = 0.0
     iters_l = iters_2 = 0
-    for k, kind in enumerate(kinds):
+    for k, kind in enumerate(HELD_OUT):
         A = synthetic.test_matrix(n, n, kind, 10 ** 6 + k, 2 * 10 ** 6 + k)
         s = np.linalg.svd(A, compute_uv=False)
         dA = dev(A)
         T = rutv.colmajor_empty(n, n)
         U = rutv.colmajor_empty(n, n)
         V = rutv.colmajor_empty(n, n)
-        rutv.factor(dA, b, 2, k)                       # warm-up
+        rutv.factor(dA, b, 2, k)                       # warm-up of both paths
+        rutv.randutv_factor_learnedq(n, n, dA, n, b, model, k, U, T, V)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r, qu = rutv.randutv_factor_learnedq(n, n, dA, n, b, model, k, U, T, V)
         torch.cuda.synchronize()
-        t_l += time.perf_counter() - t0
+        dt_l = time.perf_counter() - t0
         assert r == 0
         t0 = time.perf_counter()
         U2, T2, V2 = rutv.factor(dA, b, 2, k)
         torch.cuda.synchronize()
-        t_2 += time.perf_counter() - t0
-        iters_l += sum(x for x in qu if x >= 0)
-        iters_2 += 2 * sum(1 for x in qu if x >= 0)
+        dt_2 = time.perf_counter() - t0
+        t_l += dt_l
+        t_2 += dt_2
+        il = sum(x for x in qu if x >= 0)
+        i2 = 2 * sum(1 for x in qu if x >= 0)
+        iters_l += il
+        iters_2 += i2
         Th, T2h = host(T), host(T2)
         nrm = np.linalg.norm(A)
         assert np.linalg.norm(A - host(U) @ Th @ host(V).T) / nrm <= utv_bound(n)
@@ -175,8 +205,9 @@ def test_trained_network_gain_over_q2(rutv):
         r_2 = np.diag(T2h)[keep] / s[keep]
         dev_ = np.abs(r_l / r_2 - 1)
         ok = (dev_ <= 0.05) | (np.abs(np.log(r_l)) <= np.abs(np.log(r_2)))
-        print("%s: q used %s, max dev %.3g, %.4f of indices within 5%% (or better)"
-              % (kind, qu, dev_.max(), ok.mean()))
-        assert ok.mean() >= 0.98, kind
-    print("learned-q: %d vs %d power iterations, %.3f s vs %.3f s" % (iters_l, iters_2, t_l, t_2))
-    assert iters_l <= iters_2
+        print("learned-q %s: q used %s; %d vs %d iterations, %.4f s vs %.4f s; max dev %.3g; "
+              "%d of %d indices fail" % (kind, qu, il, i2, dt_l, dt_2, dev_.max(), int((~ok).sum()), ok.size))
+        assert ok.all(), kind
+    print("learned-q total: %d vs %d power iterations, %.3f s vs %.3f s" % (iters_l, iters_2, t_l, t_2))
+    assert iters_l < iters_2
+    assert t_l < t_2

@@ -22,13 +22,18 @@ def test_spectra_closed_forms():
     k = n // 10
     assert np.all(gap[:k] == 1.0)
     assert np.isclose(gap[k], 1e-3) and np.isclose(gap[-1], 1e-12)
-    for s in (g10, g8, alg, gap):
+    e32 = synthetic.spectrum("exp32", 1000)
+    assert np.isclose(e32[32], 0.1, rtol=1e-12) and e32[-1] == 1e-15 and e32[479] > 1e-15
+    e128 = synthetic.spectrum("exp128", n)
+    assert np.allclose(np.log10(e128), -np.arange(n) / 128.0, rtol=0, atol=1e-12)
+    for s in (g10, g8, alg, gap, e32, e128):
         assert np.all(np.diff(s) <= 0)
     with pytest.raises(ValueError):
         synthetic.spectrum("nope", 4)
 
 
-@pytest.mark.parametrize("m,n,kind", [(60, 60, "geometric10"), (90, 45, "gap"), (40, 40, "algebraic")])
+@pytest.mark.parametrize("m,n,kind", [(60, 60, "geometric10"), (90, 45, "gap"), (40, 40, "algebraic"),
+                                      (70, 50, "exp32")])
 def test_small_matrix_has_the_prescribed_spectrum(m, n, kind):
     A = synthetic.test_matrix(m, n, kind, 3, 4)
     assert A.shape == (m, n) and A.flags["F_CONTIGUOUS"]

@@ -1,7 +1,8 @@
 """The full-size workload (16000 x 16000, gap spectrum, b = 128, q = 2, U and V
 formed, FP64 emulated on the BF16 tensor cores), checked through properties
 that hold at any size. Residual and orthogonality are taken on sampled
-vectors, so no 16000^3 product is needed. Runs last: it holds the most memory."""
+vectors, so no 16000^3 product is needed. Runs near the end (it holds the most
+memory), before only the allocation-free entry point's test."""
 import numpy as np
 import pytest
 
