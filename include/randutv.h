@@ -249,7 +249,7 @@ randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64
  * Learned power-iteration count.  Sec. 3.2.1 uses a fixed q; here, before the
  * sketch of every block step, a small network (16 -> 64 -> 64 -> 4, GELU,
  * FP32, softmax over q in {0,1,2,3}) picks q from 16 features: the decay of
- * the previous block's diagonal and of the Householder R diagonal of the
+ * the previous block's panel-QR R diagonal and of the Householder R diagonal of the
  * q = 0 sketch (compressed to 2b rows by a second Gaussian sketch, a
  * subspace embedding), each as log10(|d_j| / |d_0|) at j = 0, w/8, ..., 7w/8.
  * The q = 0 product is reused by the chosen iterations.
@@ -267,7 +267,7 @@ randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64
  * kernels return at once when the chosen q is smaller, so the host never
  * waits for a block step; q_used is filled once, when the call ends.  Each
  * block's b x b SVD overlaps the next step on a side stream, as in the
- * fixed-q path; the next step's features wait only for its singular values.
+ * fixed-q path (the features need only the previous panel's R diagonal).
  */
 int randutv_learnq_model_floats(void);
 randutv_status randutv_factor_learnedq(int64_t m, int64_t n, const double* A, int64_t lda, int b,

@@ -138,12 +138,13 @@ size_t oz_operand_bytes(int64_t R, int64_t K);
 cudaError_t oz_split(bool trans, const double* X, int64_t ldx, int64_t R, int64_t K, void* buf, OzOperand* out,
                      int* status, cudaStream_t st);
 // C (M x N) = alpha La(a_row0 : a_row0 + M, :) Lb(b_row0 : b_row0 + N, :)^T + beta C
-// from split operands; needs M >= 128, N >= 64, K >= 64; P holds the FP64
-// split-K partials (p_bytes bytes; too few bytes means no split-K).
+// from split operands; needs operands of at least 16 (La) and 4 (Lb) rows,
+// and, when K < 64, both split with the same ldq; P holds the FP64 split-K
+// partials (p_bytes bytes; too few bytes means no split-K).
 cudaError_t oz_product(const OzOperand& a, int64_t a_row0, const OzOperand& b, int64_t b_row0, int64_t M, int64_t N,
                        double alpha, double beta, double* C, int64_t ldc, double* P, size_t p_bytes, int sms,
                        int* status, cudaStream_t st);
-// Needs M >= 128, N >= 64, K >= 64; `work` holds oz_work_bytes(M, N, K) bytes
+// Needs M >= 16, N >= 4, K >= 1; `work` holds oz_work_bytes(M, N, K) bytes
 // (digits, exponents and the FP64 split-K partials).
 cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
                     const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work, size_t work_bytes,

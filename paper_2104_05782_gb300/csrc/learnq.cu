@@ -6,9 +6,11 @@
 // (mu, sd) stored in the model.  Parameter layout (row-major, x W):
 //   W1[16][64] b1[64] W2[64][64] b2[64] W3[64][4] b3[4] mu[16] sd[16]
 // Features of block step i (written by k_learnq_features):
-//   f[0..7]  = log10(|d_j| / |d_0|) of the previous diagonal block d (the
-//              singular values its b x b SVD produced) at j = 0, w/8, ...,
-//              7w/8 (block 0: copies of f[8..15]);
+//   f[0..7]  = log10(|d_j| / |d_0|) of the previous block's d: the diagonal
+//              of the R its panel QR produced (|R_jj| tracks the block's
+//              singular values, and is ready before the block's b x b SVD, so
+//              that SVD can overlap the next step) at j = 0, w/8, ..., 7w/8
+//              (block 0: copies of f[8..15]);
 //   f[8..15] = log10(|R_jj| / |R_00|) at the same j, with R the Householder
 //              R of the q = 0 sketch Y0 = T22^T G compressed to at most 2b
 //              rows by a second Gaussian sketch (Omega Y0, Omega 2b x n'; a

@@ -71,6 +71,7 @@ struct Workspace {
     float* feat;      // 16 features of the current block
     int* qdev;        // chosen q
     double* dq;       // candidate diagonals, 4 x w (trace mode)
+    double* rdiag;    // learned q / trace: the R diagonal of the last panel QR (w)
     float* qmodel;    // network parameters on the device
     void* oz;         // digit slices and exponents of the emulated FP64 products
     size_t oz_bytes;
@@ -92,6 +93,7 @@ struct Layout {
     size_t off[kSlots];
     size_t total;
     size_t part_elems;
+    int64_t wmax;  // the widest block: min(b, n)
 };
 
 int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
@@ -175,7 +177,7 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec, bool qr_first
         lp ? sizeof(float) * (size_t)mx * npad : 0,                 // Y / Z in FP32
         lp ? sizeof(float) * cholqr_scratch_floats((int)npad, sms) : 0,
         lp ? sizeof(unsigned long long) : 0,                        // max |T22|
-        sizeof(float) * 32 + sizeof(double) * 4 * (size_t)wmax,     // learned-q features, q, candidates
+        sizeof(float) * 32 + sizeof(double) * 5 * (size_t)wmax,     // learned-q features, q, candidates, R diagonal
         sizeof(float) * (size_t)learnq_nparam(),                    // learned-q model
         emulated_prec(prec) ? oz_work_bytes(mx, std::max<int64_t>(wmax, 128), mx) : 0,   // Ozaki digits
         emulated_prec(prec) ? oz_operand_bytes(m, n) : 0,                               // T(:, k0:n) by rows
@@ -194,6 +196,7 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec, bool qr_first
     }
     L.total = o;
     L.part_elems = part;
+    L.wmax = wmax;
     return L;
 }
 
@@ -230,6 +233,7 @@ Workspace carve(void* base, const Layout& L) {
     w.feat = (float*)(p + L.off[26]);
     w.qdev = (int*)(w.feat + 16);
     w.dq = (double*)(p + L.off[26] + sizeof(float) * 32);
+    w.rdiag = w.dq + 4 * (size_t)L.wmax;
     w.qmodel = (float*)(p + L.off[27]);
     w.oz = (void*)(p + L.off[28]);
     w.oz_bytes = L.off[29] - L.off[28];
@@ -485,9 +489,63 @@ cudaError_t defer_put(Ctx& c, const double* src, int64_t lds, int64_t rows, int6
 // side stream, room is left for its 16-block cluster and the FP32 block.
 int panel_sms(const Ctx& c) { return (c.overlap && c.sms > 64) ? c.sms - 17 : c.sms; }
 
+// Sub-panel width of the blocked panel QR (emulated products only).
+constexpr int kSubPanel = 32;
+
+// A product of the blocked panel: emulated on the tensor cores when the
+// emulated precision is selected (skinny shapes allowed), else FP64 DMMA.
+cudaError_t panel_gemm(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                       int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
+    if (emulated_prec(c.prec) && M >= 16 && N >= 8 && K >= 8)
+        return oz_gemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.w.oz, c.w.oz_bytes, c.sms, c.w.status,
+                       c.st);
+    return gemm_f64(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.w.part, c.w.part_elems, c.sms, c.st);
+}
+
+// Blocked Householder QR of a len x w panel (the recursion-free form of
+// LAPACK's blocked QR, Sec. 2.3): sub-panels of kSubPanel columns are factored
+// by the one-barrier-per-column kernel, and each one's compact WY transform
+// Q_k = I - W_k Tf_k W_k^T is applied to the columns right of it,
+// C := Q_k^T C = C - W_k Tf_k^T (W_k^T C), by three products.  Most of the
+// panel's FP64 multiply-adds thus move into those products (emulated on the
+// tensor cores); the reflectors, tau and R are those of the unblocked
+// factorization, up to rounding.  Uses c.w.W and c.w.Tf as scratch
+// (factor_panel recomputes W, Tf of the whole panel afterwards) and keeps the
+// sub-panel's Gram matrix and the two wk x rest products in c.w.gram:
+// wk^2 + 2 wk (w - wk) <= w^2 for every w.
+cudaError_t blocked_panel_qr(Ctx& c, double* P, int64_t ld, int64_t len, int w) {
+    for (int k0 = 0; k0 < w; k0 += kSubPanel) {
+        const int wk = std::min(kSubPanel, w - k0);
+        const int64_t lk = len - k0;
+        double* Pk = P + k0 + (int64_t)k0 * ld;
+        {
+            TraceScope ts("panel_qr", 2.0 * (double)lk * wk * wk, 16.0 * (double)lk * wk, c.st);
+            CK(panel_qr(Pk, ld, lk, wk, c.w.tau + k0, c.w.pscr, c.w.bars, c.w.status, panel_sms(c), c.st));
+        }
+        const int rest = w - k0 - wk;
+        if (rest <= 0 || lk <= 0) continue;
+        TraceScope ts("panel_update", 4.0 * (double)lk * wk * (wk + rest), 8.0 * (double)lk * (2 * wk + 2 * rest),
+                      c.st);
+        double* C = Pk + (int64_t)wk * ld;
+        double* Gk = c.w.gram;
+        double* Xk = Gk + (size_t)wk * wk;
+        double* X2k = Xk + (size_t)wk * rest;
+        CK(extract_w(Pk, ld, lk, wk, c.w.W, c.st));
+        CK(panel_gemm(c, true, false, wk, wk, lk, 1.0, c.w.W, lk, c.w.W, lk, 0.0, Gk, wk));
+        CK(tfactor(Gk, c.w.tau + k0, wk, c.w.Tf, c.w.status, c.st));
+        CK(panel_gemm(c, true, false, wk, rest, lk, 1.0, c.w.W, lk, C, ld, 0.0, Xk, wk));
+        CK(gemm_f64(true, false, wk, rest, wk, 1.0, c.w.Tf, wk, Xk, wk, 0.0, X2k, wk, c.w.part, c.w.part_elems, c.sms,
+                    c.st));
+        CK(panel_gemm(c, false, false, lk, rest, wk, -1.0, c.w.W, lk, X2k, wk, 1.0, C, ld));
+    }
+    return cudaSuccess;
+}
+
 // Householder QR of a len x w panel plus its W (explicit) and Tf.
 cudaError_t factor_panel(Ctx& c, double* P, int64_t ld, int64_t len, int w) {
-    {
+    if (emulated_prec(c.prec) && w > kSubPanel && len >= 1024) {
+        CK(blocked_panel_qr(c, P, ld, len, w));
+    } else {
         TraceScope ts("panel_qr", 2.0 * (double)len * w * w, 16.0 * (double)len * w, c.st);
         CK(panel_qr(P, ld, len, w, c.w.tau, c.w.pscr, c.w.bars, c.w.status, panel_sms(c), c.st));
     }
@@ -702,6 +760,8 @@ cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
     double* T = c.T;
     double* P = T + k0 + k0 * ldt;
     CK(factor_panel(c, P, ldt, mp, w));
+    if (c.mode != MODE_FIXED)  // the learned-q features of the next step read this panel's R diagonal
+        CK(copy_matrix(P, ldt + 1, c.w.rdiag, 1, 1, w, c.st));
     if (c.steps.empty() || c.steps.back().k0 != k0) c.steps.push_back(Ctx::Step{k0, w, false, 0, 0, 0, 0, 0, 0});
     c.steps.back().w = w;
     if (c.overlap) {
@@ -892,8 +952,8 @@ constexpr int64_t kFeatureDrawStep = (int64_t)1 << 40;
 
 // Features of block step i (needs Y0 = T22^T G in c.w.Y): the Householder R
 // of E = Omega Y0 (2b x b, two Gaussian draws Omega_1, Omega_2 of b rows each;
-// E = Y0 when n' <= 2b) and the previous block's diagonal, read from
-// dprev[j * dstride].
+// E = Y0 when n' <= 2b) and the previous block's R diagonal (from its panel
+// QR), read from dprev[j * dstride].
 cudaError_t block_features(Ctx& c, int64_t i, int64_t np, const double* dprev, int64_t dstride) {
     const int b = c.b;
     TraceScope ts("learnq_features", 4.0 * (double)np * b * b, 16.0 * (double)np * b, c.st);
@@ -980,8 +1040,7 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
         CK(fp64_iterate(c, k0, c.w.Y, 2));
     } else if (c.mode == MODE_TRACE) {
         CK(fp64_begin(c, i, k0));
-        const int64_t p0 = k0 - b;  // the previous diagonal block, already in T (serial mode)
-        CK(block_features(c, i, np, k0 > 0 ? c.T + p0 + p0 * ldt : nullptr, ldt + 1));
+        CK(block_features(c, i, np, k0 > 0 ? c.w.rdiag : nullptr, 1));
         CK(trace_candidates(c, k0));
         if (c.tr_count < c.tr_max) {
             double cand[4 * 512];
@@ -1020,20 +1079,9 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
         } else {
             CK(fp64_begin(c, i, k0));
         }
-        // the previous block's diagonal: its SVD's D once that SVD is done
-        // (overlapped on the side stream), or T's diagonal (serial)
-        const double* dprev = nullptr;
-        int64_t dstride = 1;
-        if (k0 > 0 && c.overlap) {
-            SideStream* ss = nullptr;
-            CK(side_stream(&ss));
-            CK(cudaStreamWaitEvent(c.st, ss->svd_done, 0));
-            dprev = c.w.D;
-        } else if (k0 > 0) {
-            dprev = c.T + (k0 - b) * (ldt + 1);
-            dstride = ldt + 1;
-        }
-        CK(block_features(c, i, np, dprev, dstride));
+        // the previous block's decay: the R diagonal of its panel QR, ready
+        // before its small SVD (which keeps overlapping this step)
+        CK(block_features(c, i, np, k0 > 0 ? c.w.rdiag : nullptr, 1));
         CK(learnq_infer(c.have_model ? c.w.qmodel : nullptr, c.w.feat, c.q, c.w.qdev, c.w.qlog + i, c.st));
         if (!lowp) CK(prefetch_splits(c, k0));
         // every iteration up to q = 3 is queued; the kernels of iteration it

@@ -117,7 +117,8 @@ def test_trace_labels_follow_definition(rutv):
     r, F, y, cand = rutv.randutv_learnq_trace(m, n, dev(A), m, b, 4, T, candidates=True)
     assert r == 0 and len(y) == n // b - 1
     assert np.all(np.isfinite(F))
-    assert np.all(F[:, :8] <= 1e-6)  # previous diagonal block: sorted descending
+    # block 0 has no previous block: its first half copies the sketch half
+    assert np.array_equal(F[0, :8], F[0, 8:]) and F[0, 8] == 0.0
     # the q = 2 candidate diagonal is the diagonal the q = 2 trajectory produces
     Tt = host(T)
     _, Tf, _ = rutv.factor(dev(A), b, 2, 4, want_uv=False)
