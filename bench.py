@@ -710,7 +710,10 @@ def run_batched(args, rank: int, world: int, local_rank: int):
     plan = rutv.BatchPlan(ms, ns, A, ms, U, T, V, seeds, q, prec, table)
     b_of = {}
     for line in table.strip().splitlines():
-        lo, hi, tall, b = map(int, line.split())
+        f = line.split()
+        if f[0] == "threads":
+            continue
+        lo, hi, tall, b = map(int, f[:4])
         b_of[(lo, hi, tall)] = b
     F = 0.0
     for k in range(count):

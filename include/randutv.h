@@ -210,10 +210,13 @@ randutv_status randutv_factor_host(int64_t m, int64_t n, const double* A, int64_
  *                     (m x m / n x n) or NULL (no orthonormal factors).
  *   q               : power-iteration count for every matrix.
  *   prec            : RANDUTV_FP64 or RANDUTV_SKETCH_FP32.
- *   autotune_table  : text with lines "nmin nmax tall b" (tall: 1 = m > n,
- *                     0 = square, -1 = any), e.g. the output of
- *                     randutv_batched_autotune; NULL = built-in table.
- *                     Block sizes are clamped to [1, 64].
+ *   autotune_table  : text with lines "nmin nmax tall b [tile]" (tall: 1 =
+ *                     m > n, 0 = square, -1 = any; tile: the output tile of
+ *                     the per-matrix DMMA products, 32 or 64, default 64)
+ *                     and an optional line "threads NT" (threads per CTA,
+ *                     i.e. per matrix in flight: 128 or 256, default 256),
+ *                     e.g. the output of randutv_batched_autotune; NULL =
+ *                     built-in table.  Block sizes are clamped to [1, 64].
  *   status          : host array of count statuses (or NULL), filled on return.
  * randutv_batched builds a plan, runs it once and frees it (synchronous).
  * A plan keeps the descriptors on the device and holds the launch as a CUDA
@@ -236,9 +239,11 @@ void randutv_batched_plan_destroy(randutv_batch_plan* plan);
 /*
  * randutv_batched_autotune: for each size class (n in [2^k, 2^(k+1)), square
  * and tall separately) times the batched kernel on up to 608 members of the
- * class with b = 16, 32 and 64 and writes the fastest as a table (the format
- * randutv_batched reads) into table_out (host, table_bytes bytes).  Overwrites
- * T, U, V of the matrices it runs.  Synchronous.
+ * class with b = 16, 32, 64 and GEMM tiles of 32 and 64, keeps the fastest,
+ * then times the whole batch with 128 and 256 threads per matrix, and writes
+ * the result as a table (the format randutv_batched reads) into table_out
+ * (host, table_bytes bytes).  Overwrites T, U, V of the matrices it runs.
+ * Synchronous.
  */
 randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64_t* n, const double* const* A,
                                         const int64_t* lda, double* const* U, double* const* T, double* const* V,

@@ -13,6 +13,11 @@
 // path (Gaussian draw, signs, ordering), so each matrix matches the oracle.
 // Nothing waits on another CTA: the queue pop is one atomicAdd.
 //
+// Tunable shape: the engine is compiled for 128 and 256 threads per CTA
+// (threads per matrix in flight, one choice per plan), and its DMMA GEMM for
+// 32 x 32 and 64 x 64 output tiles (chosen per matrix); with the block size
+// b per size class, randutv_batched_autotune times these choices.
+//
 // The optional FP32 sketch (RANDUTV_SKETCH_FP32) runs the sketch products on
 // the FP32 pipe (about 70x the FP64 rate on GB300) with an FP32 classical
 // Gram-Schmidt (twice) re-orthonormalisation between products; the rest is FP64.
@@ -33,8 +38,8 @@ namespace rutv {
 
 namespace {
 
-constexpr int BNT = 256;  // threads per CTA
-constexpr int BNW = BNT / 32;
+constexpr int kMaxThreads = 256;  // threads per CTA: 128 or 256 (the template parameter NT)
+constexpr int kMaxWarps = kMaxThreads / 32;
 constexpr int BMAX = 64;  // largest block size of the batched path
 constexpr int kBatchedMaxSweeps = 30;
 
@@ -44,6 +49,7 @@ struct BatchDesc {
     double *U, *T, *V;
     uint64_t seed;
     int b, status;
+    int tile;  // GEMM tile of this matrix (32 or 64)
 };
 
 struct Slot {  // per-CTA workspace, sized for the largest matrix of the batch
@@ -54,7 +60,7 @@ struct Slot {  // per-CTA workspace, sized for the largest matrix of the batch
 struct BSmem {
     double As[16][64 + 2];
     double Bs[16][64 + 2];
-    double red[BNW * 3];
+    double red[kMaxWarps * 3];
     double wv[BMAX + 2];
     double sc[4];
     double jA[BMAX * BMAX];
@@ -68,34 +74,40 @@ __device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
                  : "d"(a), "d"(b));
 }
 
-// C = alpha op(A) op(B) + beta C over the whole CTA, 64 x 64 tiles, 8 warps of
-// 32 x 16 (4 x 2 m8n8k4 fragments).
-template <bool TA, bool TB>
+// C = alpha op(A) op(B) + beta C over the whole CTA of NT threads (128 or
+// 256), TILE x TILE output tiles (32 or 64), 16-deep k steps staged in shared
+// memory.  The warps form a 2 x (NT / 64) grid, each owning a
+// (TILE / 2) x (2 TILE / (NT / 32)) block of m8n8k4 DMMA fragments.
+template <bool TA, bool TB, int TILE, int NT>
 __device__ void cta_gemm(int M, int N, int K, double alpha, const double* A, int64_t lda, const double* B,
                          int64_t ldb, double beta, double* C, int64_t ldc, BSmem& sm) {
+    constexpr int BNW = NT / 32;
+    constexpr int WR = TILE / 2, WC = 2 * TILE / BNW, FI = WR / 8, FJ = WC / 8;
+    constexpr int LOADS = TILE * 16 / NT;  // elements of each operand tile per thread and k step
+    static_assert(FI >= 1 && FJ >= 1 && LOADS >= 1, "tile and thread count");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp & 1) * 32, wn = (warp >> 1) * 16;
-    const int tm = (M + 63) / 64, tn = (N + 63) / 64;
+    const int wm = (warp & 1) * WR, wn = (warp >> 1) * WC;
+    const int tm = (M + TILE - 1) / TILE, tn = (N + TILE - 1) / TILE;
     for (int t = 0; t < tm * tn; ++t) {
-        const int row0 = (t % tm) * 64, col0 = (t / tm) * 64;
-        double acc[4][2][2];
+        const int row0 = (t % tm) * TILE, col0 = (t / tm) * TILE;
+        double acc[FI][FJ][2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < FI; ++i)
 #pragma unroll
-            for (int j = 0; j < 2; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+            for (int j = 0; j < FJ; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
         for (int k0 = 0; k0 < K; k0 += 16) {
             __syncthreads();
 #pragma unroll
-            for (int it = 0; it < 4; ++it) {
-                int idx = tid + it * BNT;
+            for (int it = 0; it < LOADS; ++it) {
+                int idx = tid + it * NT;
                 int m, k;
-                if (!TA) { m = idx % 64; k = idx / 64; } else { k = idx % 16; m = idx / 16; }
+                if (!TA) { m = idx % TILE; k = idx / TILE; } else { k = idx % 16; m = idx / 16; }
                 int gi = row0 + m, gk = k0 + k;
                 double v = 0.0;
                 if (gi < M && gk < K) v = TA ? A[gk + (int64_t)gi * lda] : A[gi + (int64_t)gk * lda];
                 sm.As[k][m] = v;
                 int n, kk;
-                if (TB) { n = idx % 64; kk = idx / 64; } else { kk = idx % 16; n = idx / 16; }
+                if (TB) { n = idx % TILE; kk = idx / TILE; } else { kk = idx % 16; n = idx / 16; }
                 int gj = col0 + n, gk2 = k0 + kk;
                 double u = 0.0;
                 if (gj < N && gk2 < K) u = TB ? B[gj + (int64_t)gk2 * ldb] : B[gk2 + (int64_t)gj * ldb];
@@ -104,23 +116,23 @@ __device__ void cta_gemm(int M, int N, int K, double alpha, const double* A, int
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < 16; kk += 4) {
-                double af[4], bf[2];
+                double af[FI], bf[FJ];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) af[i] = sm.As[kk + (lane & 3)][wm + i * 8 + (lane >> 2)];
+                for (int i = 0; i < FI; ++i) af[i] = sm.As[kk + (lane & 3)][wm + i * 8 + (lane >> 2)];
 #pragma unroll
-                for (int j = 0; j < 2; ++j) bf[j] = sm.Bs[kk + (lane & 3)][wn + j * 8 + (lane >> 2)];
+                for (int j = 0; j < FJ; ++j) bf[j] = sm.Bs[kk + (lane & 3)][wn + j * 8 + (lane >> 2)];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < FI; ++i)
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) dmma(acc[i][j], af[i], bf[j]);
+                    for (int j = 0; j < FJ; ++j) dmma(acc[i][j], af[i], bf[j]);
             }
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < FI; ++i) {
             int gi = row0 + wm + i * 8 + (lane >> 2);
             if (gi >= M) continue;
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
+            for (int j = 0; j < FJ; ++j)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     int gj = col0 + wn + j * 8 + 2 * (lane & 3) + h;
@@ -134,16 +146,28 @@ __device__ void cta_gemm(int M, int N, int K, double alpha, const double* A, int
     __syncthreads();
 }
 
-__device__ void cta_gemm_dispatch(bool ta, bool tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
-                                  const double* B, int64_t ldb, double beta, double* C, int64_t ldc, BSmem& sm) {
-    if (M <= 0 || N <= 0) return;
-    if (!ta && !tb) cta_gemm<false, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
-    else if (ta && !tb) cta_gemm<true, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
-    else if (!ta && tb) cta_gemm<false, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
-    else cta_gemm<true, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+template <int NT, int TILE>
+__device__ void cta_gemm_t(bool ta, bool tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
+                           const double* B, int64_t ldb, double beta, double* C, int64_t ldc, BSmem& sm) {
+    if (!ta && !tb) cta_gemm<false, false, TILE, NT>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+    else if (ta && !tb) cta_gemm<true, false, TILE, NT>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+    else if (!ta && tb) cta_gemm<false, true, TILE, NT>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+    else cta_gemm<true, true, TILE, NT>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
 }
 
+// tile: the matrix's GEMM tile (32 or 64), chosen per matrix by the autotune table
+template <int NT>
+__device__ void cta_gemm_dispatch(int tile, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
+                                  int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                                  BSmem& sm) {
+    if (M <= 0 || N <= 0) return;
+    if (tile == 32) cta_gemm_t<NT, 32>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+    else cta_gemm_t<NT, 64>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+}
+
+template <int NT>
 __device__ double block_sum(double v, BSmem& sm) {
+    constexpr int BNW = NT / 32;
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
@@ -155,7 +179,9 @@ __device__ double block_sum(double v, BSmem& sm) {
 }
 
 // Householder QR of P (len x w, ld), dlarfg rule (as the panel kernel).
+template <int NT>
 __device__ void cta_householder(double* P, int64_t ld, int len, int w, double* tau, int* status, BSmem& sm) {
+    constexpr int BNT = NT, BNW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int j = 0; j < w && j < len; ++j) {
         double s = 0.0;
@@ -163,7 +189,7 @@ __device__ void cta_householder(double* P, int64_t ld, int len, int w, double* t
             double x = P[r + (int64_t)j * ld];
             s += x * x;
         }
-        const double xi2 = block_sum(s, sm);
+        const double xi2 = block_sum<NT>(s, sm);
         const double alpha = P[j + (int64_t)j * ld];
         double tj = 0.0, beta = alpha, d = 1.0;
         bool act = false;
@@ -200,7 +226,9 @@ __device__ void cta_householder(double* P, int64_t ld, int len, int w, double* t
     __syncthreads();
 }
 
+template <int NT>
 __device__ void cta_extract_w(const double* P, int64_t ld, int len, int w, double* W) {
+    constexpr int BNT = NT;
     for (int e = threadIdx.x; e < len * w; e += BNT) {
         int r = e % len, c = e / len;
         W[e] = (r < c) ? 0.0 : (r == c ? 1.0 : P[r + (int64_t)c * ld]);
@@ -209,7 +237,9 @@ __device__ void cta_extract_w(const double* P, int64_t ld, int len, int w, doubl
 }
 
 // Tf(j,j) = tau_j, Tf(0:j, j) = -tau_j Tf(0:j,0:j) gram(0:j, j)  (Sec. 2.3)
+template <int NT>
 __device__ void cta_tfactor(const double* gram, const double* tau, int w, double* Tf) {
+    constexpr int BNT = NT, BNW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < w * w; e += BNT) Tf[e] = 0.0;
     __syncthreads();
@@ -228,8 +258,10 @@ __device__ void cta_tfactor(const double* gram, const double* tau, int w, double
 
 // One-sided Jacobi SVD of the upper triangle of R (w x w, w <= BMAX) in shared
 // memory; circle ordering, one warp per pair; canonical output as svd.cu.
+template <int NT>
 __device__ void cta_jacobi(const double* R, int64_t ldr, int w, double* D, double* Us, double* Vs, int* status,
                            BSmem& sm) {
+    constexpr int BNT = NT, BNW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double* A = sm.jA;
     double* V = sm.jV;
@@ -346,7 +378,9 @@ __device__ void cta_jacobi(const double* R, int64_t ldr, int w, double* D, doubl
     __syncthreads();
 }
 
+template <int NT>
 __device__ void cta_copy(const double* src, int64_t lds, double* dst, int64_t ldd, int rows, int cols) {
+    constexpr int BNT = NT;
     for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += BNT) {
         int64_t i = e % rows, j = e / rows;
         dst[i + j * ldd] = src[i + j * lds];
@@ -356,51 +390,56 @@ __device__ void cta_copy(const double* src, int64_t lds, double* dst, int64_t ld
 
 struct MatCtx {
     int64_t m, n;
-    int b, q, prec;
+    int b, q, prec, tile;
     uint64_t seed;
     double *U, *T, *V;
     Slot s;
     int* status;
 };
 
+template <int NT>
 __device__ void b_factor_panel(MatCtx& c, double* P, int64_t ld, int len, int w, BSmem& sm) {
-    cta_householder(P, ld, len, w, c.s.tau, c.status, sm);
-    cta_extract_w(P, ld, len, w, c.s.W);
-    cta_gemm_dispatch(true, false, w, w, len, 1.0, c.s.W, len, c.s.W, len, 0.0, c.s.gram, w, sm);
-    cta_tfactor(c.s.gram, c.s.tau, w, c.s.Tf);
+    cta_householder<NT>(P, ld, len, w, c.s.tau, c.status, sm);
+    cta_extract_w<NT>(P, ld, len, w, c.s.W);
+    cta_gemm_dispatch<NT>(c.tile, true, false, w, w, len, 1.0, c.s.W, len, c.s.W, len, 0.0, c.s.gram, w, sm);
+    cta_tfactor<NT>(c.s.gram, c.s.tau, w, c.s.Tf);
 }
 
+template <int NT>
 __device__ void b_apply_right(MatCtx& c, double* C, int64_t ldc, int rows, int cols, int w, BSmem& sm) {
     if (rows <= 0 || cols <= 0) return;
-    cta_gemm_dispatch(false, false, rows, w, cols, 1.0, C, ldc, c.s.W, cols, 0.0, c.s.X, rows, sm);
-    cta_gemm_dispatch(false, false, rows, w, w, 1.0, c.s.X, rows, c.s.Tf, w, 0.0, c.s.X2, rows, sm);
-    cta_gemm_dispatch(false, true, rows, cols, w, -1.0, c.s.X2, rows, c.s.W, cols, 1.0, C, ldc, sm);
+    cta_gemm_dispatch<NT>(c.tile, false, false, rows, w, cols, 1.0, C, ldc, c.s.W, cols, 0.0, c.s.X, rows, sm);
+    cta_gemm_dispatch<NT>(c.tile, false, false, rows, w, w, 1.0, c.s.X, rows, c.s.Tf, w, 0.0, c.s.X2, rows, sm);
+    cta_gemm_dispatch<NT>(c.tile, false, true, rows, cols, w, -1.0, c.s.X2, rows, c.s.W, cols, 1.0, C, ldc, sm);
 }
 
+template <int NT>
 __device__ void b_apply_left_t(MatCtx& c, double* C, int64_t ldc, int len, int cols, int w, BSmem& sm) {
     if (len <= 0 || cols <= 0) return;
-    cta_gemm_dispatch(true, false, w, cols, len, 1.0, c.s.W, len, C, ldc, 0.0, c.s.X, w, sm);
-    cta_gemm_dispatch(true, false, w, cols, w, 1.0, c.s.Tf, w, c.s.X, w, 0.0, c.s.X2, w, sm);
-    cta_gemm_dispatch(false, false, len, cols, w, -1.0, c.s.W, len, c.s.X2, w, 1.0, C, ldc, sm);
+    cta_gemm_dispatch<NT>(c.tile, true, false, w, cols, len, 1.0, c.s.W, len, C, ldc, 0.0, c.s.X, w, sm);
+    cta_gemm_dispatch<NT>(c.tile, true, false, w, cols, w, 1.0, c.s.Tf, w, c.s.X, w, 0.0, c.s.X2, w, sm);
+    cta_gemm_dispatch<NT>(c.tile, false, false, len, cols, w, -1.0, c.s.W, len, c.s.X2, w, 1.0, C, ldc, sm);
 }
 
+template <int NT>
 __device__ void b_panel_and_svd(MatCtx& c, int64_t k0, int w, BSmem& sm) {
+    constexpr int BNT = NT;
     const int m = (int)c.m, n = (int)c.n;
     const int mp = m - (int)k0;
     double* T = c.T;
     double* P = T + k0 + k0 * m;
-    b_factor_panel(c, P, m, mp, w, sm);
-    b_apply_left_t(c, T + k0 + (k0 + w) * m, m, mp, n - (int)k0 - w, w, sm);
-    if (c.U) b_apply_right(c, c.U + k0 * m, m, m, mp, w, sm);
-    cta_jacobi(P, m, w, c.s.D, c.s.Us, c.s.Vs, c.status, sm);
+    b_factor_panel<NT>(c, P, m, mp, w, sm);
+    b_apply_left_t<NT>(c, T + k0 + (k0 + w) * m, m, mp, n - (int)k0 - w, w, sm);
+    if (c.U) b_apply_right<NT>(c, c.U + k0 * m, m, m, mp, w, sm);
+    cta_jacobi<NT>(P, m, w, c.s.D, c.s.Us, c.s.Vs, c.status, sm);
     if (k0 > 0) {
-        cta_gemm_dispatch(false, false, (int)k0, w, w, 1.0, T + k0 * m, m, c.s.Vs, w, 0.0, c.s.tmp, k0, sm);
-        cta_copy(c.s.tmp, k0, T + k0 * m, m, (int)k0, w);
+        cta_gemm_dispatch<NT>(c.tile, false, false, (int)k0, w, w, 1.0, T + k0 * m, m, c.s.Vs, w, 0.0, c.s.tmp, k0, sm);
+        cta_copy<NT>(c.s.tmp, k0, T + k0 * m, m, (int)k0, w);
     }
     const int nr = n - (int)k0 - w;
     if (nr > 0) {
-        cta_gemm_dispatch(true, false, w, nr, w, 1.0, c.s.Us, w, T + k0 + (k0 + w) * m, m, 0.0, c.s.tmp, w, sm);
-        cta_copy(c.s.tmp, w, T + k0 + (k0 + w) * m, m, w, nr);
+        cta_gemm_dispatch<NT>(c.tile, true, false, w, nr, w, 1.0, c.s.Us, w, T + k0 + (k0 + w) * m, m, 0.0, c.s.tmp, w, sm);
+        cta_copy<NT>(c.s.tmp, w, T + k0 + (k0 + w) * m, m, w, nr);
     }
     for (int64_t e = threadIdx.x; e < (int64_t)mp * w; e += BNT) {
         int64_t i = e % mp, j = e / mp;
@@ -408,19 +447,21 @@ __device__ void b_panel_and_svd(MatCtx& c, int64_t k0, int w, BSmem& sm) {
     }
     __syncthreads();
     if (c.V) {
-        cta_gemm_dispatch(false, false, n, w, w, 1.0, c.V + k0 * n, n, c.s.Vs, w, 0.0, c.s.tmp, n, sm);
-        cta_copy(c.s.tmp, n, c.V + k0 * n, n, n, w);
+        cta_gemm_dispatch<NT>(c.tile, false, false, n, w, w, 1.0, c.V + k0 * n, n, c.s.Vs, w, 0.0, c.s.tmp, n, sm);
+        cta_copy<NT>(c.s.tmp, n, c.V + k0 * n, n, n, w);
     }
     if (c.U) {
-        cta_gemm_dispatch(false, false, m, w, w, 1.0, c.U + k0 * m, m, c.s.Us, w, 0.0, c.s.tmp, m, sm);
-        cta_copy(c.s.tmp, m, c.U + k0 * m, m, m, w);
+        cta_gemm_dispatch<NT>(c.tile, false, false, m, w, w, 1.0, c.U + k0 * m, m, c.s.Us, w, 0.0, c.s.tmp, m, sm);
+        cta_copy<NT>(c.s.tmp, m, c.U + k0 * m, m, m, w);
     }
 }
 
 // FP32 sketch product on CUDA cores: Out (M x b, FP32) = op(T22) In (K x b),
 // op = transpose (Y = T22^T In) or not (Z = T22 In).  T22 read in FP64.
+template <int NT>
 __device__ void cta_sgemm_sketch(bool trans, int M, int K, int b, const double* T22, int64_t ldt, const float* In,
                                  float* Out) {
+    constexpr int BNT = NT;
     for (int e = threadIdx.x; e < M * b; e += BNT) {
         int i = e % M, j = e / M;
         float s = 0.0f;
@@ -437,7 +478,9 @@ __device__ void cta_sgemm_sketch(bool trans, int M, int K, int b, const double* 
 // FP32 classical Gram-Schmidt with reorthogonalisation (CGS2) on the columns
 // of X (L x b): for each column, two passes of h = X(:,0:j)^T x_j,
 // x_j -= X(:,0:j) h, then normalisation.
+template <int NT>
 __device__ void cta_cgs2_32(float* X, int L, int b, BSmem& sm) {
+    constexpr int BNT = NT, BNW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int j = 0; j < b; ++j) {
         float* xj = X + (int64_t)j * L;
@@ -459,14 +502,16 @@ __device__ void cta_cgs2_32(float* X, int L, int b, BSmem& sm) {
         }
         float nn = 0.0f;
         for (int r = tid; r < L; r += BNT) nn = fmaf(xj[r], xj[r], nn);
-        const double tot = block_sum((double)nn, sm);
+        const double tot = block_sum<NT>((double)nn, sm);
         const float inv = tot > 0.0 ? (float)(1.0 / sqrt(tot)) : 0.0f;
         for (int r = tid; r < L; r += BNT) xj[r] *= inv;
         __syncthreads();
     }
 }
 
+template <int NT>
 __device__ void b_sketch_step(MatCtx& c, int64_t i, BSmem& sm) {
+    constexpr int BNT = NT;
     const int m = (int)c.m, n = (int)c.n, b = c.b;
     const int64_t k0 = i * (int64_t)b;
     const int mp = m - (int)k0, np = n - (int)k0;
@@ -487,29 +532,31 @@ __device__ void b_sketch_step(MatCtx& c, int64_t i, BSmem& sm) {
         float* Gf = c.s.Zf;
         for (int e = threadIdx.x; e < mp * b; e += BNT) Gf[e] = (float)c.s.G[e];
         __syncthreads();
-        cta_sgemm_sketch(true, np, mp, b, T22, m, Gf, c.s.Yf);
+        cta_sgemm_sketch<NT>(true, np, mp, b, T22, m, Gf, c.s.Yf);
         for (int it = 0; it < c.q; ++it) {
-            cta_cgs2_32(c.s.Yf, np, b, sm);
-            cta_sgemm_sketch(false, mp, np, b, T22, m, c.s.Yf, c.s.Zf);
-            cta_cgs2_32(c.s.Zf, mp, b, sm);
-            cta_sgemm_sketch(true, np, mp, b, T22, m, c.s.Zf, c.s.Yf);
+            cta_cgs2_32<NT>(c.s.Yf, np, b, sm);
+            cta_sgemm_sketch<NT>(false, mp, np, b, T22, m, c.s.Yf, c.s.Zf);
+            cta_cgs2_32<NT>(c.s.Zf, mp, b, sm);
+            cta_sgemm_sketch<NT>(true, np, mp, b, T22, m, c.s.Zf, c.s.Yf);
         }
         for (int e = threadIdx.x; e < np * b; e += BNT) c.s.Y[e] = (double)c.s.Yf[e];
         __syncthreads();
     } else {
-        cta_gemm_dispatch(true, false, np, b, mp, 1.0, T22, m, c.s.G, mp, 0.0, c.s.Y, np, sm);
+        cta_gemm_dispatch<NT>(c.tile, true, false, np, b, mp, 1.0, T22, m, c.s.G, mp, 0.0, c.s.Y, np, sm);
         for (int it = 0; it < c.q; ++it) {
-            cta_gemm_dispatch(false, false, mp, b, np, 1.0, T22, m, c.s.Y, np, 0.0, c.s.Z, mp, sm);
-            cta_gemm_dispatch(true, false, np, b, mp, 1.0, T22, m, c.s.Z, mp, 0.0, c.s.Y, np, sm);
+            cta_gemm_dispatch<NT>(c.tile, false, false, mp, b, np, 1.0, T22, m, c.s.Y, np, 0.0, c.s.Z, mp, sm);
+            cta_gemm_dispatch<NT>(c.tile, true, false, np, b, mp, 1.0, T22, m, c.s.Z, mp, 0.0, c.s.Y, np, sm);
         }
     }
-    b_factor_panel(c, c.s.Y, np, np, b, sm);
-    b_apply_right(c, c.T + k0 * m, m, m, np, b, sm);
-    if (c.V) b_apply_right(c, c.V + k0 * n, n, n, np, b, sm);
-    b_panel_and_svd(c, k0, b, sm);
+    b_factor_panel<NT>(c, c.s.Y, np, np, b, sm);
+    b_apply_right<NT>(c, c.T + k0 * m, m, m, np, b, sm);
+    if (c.V) b_apply_right<NT>(c, c.V + k0 * n, n, n, np, b, sm);
+    b_panel_and_svd<NT>(c, k0, b, sm);
 }
 
+template <int NT>
 __device__ void b_factor_one(MatCtx& c, const double* A, int64_t lda, BSmem& sm) {
+    constexpr int BNT = NT;
     const int m = (int)c.m, n = (int)c.n;
     for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += BNT) {
         int64_t i = e % m, j = e / m;
@@ -527,14 +574,15 @@ __device__ void b_factor_one(MatCtx& c, const double* A, int64_t lda, BSmem& sm)
         const int64_t np = c.n - k0;
         if (np <= 0) break;
         if (np <= c.b) {
-            b_panel_and_svd(c, k0, (int)np, sm);
+            b_panel_and_svd<NT>(c, k0, (int)np, sm);
             break;
         }
-        b_sketch_step(c, i, sm);
+        b_sketch_step<NT>(c, i, sm);
     }
 }
 
-__global__ void __launch_bounds__(BNT) k_batched(BatchDesc* desc, const int* order, int count, int q, int prec,
+template <int NT>
+__global__ void __launch_bounds__(NT) k_batched(BatchDesc* desc, const int* order, int count, int q, int prec,
                                                  double* slots, size_t slot_doubles, int64_t maxdim,
                                                  unsigned* next) {
     extern __shared__ double bsm_raw[];
@@ -574,13 +622,14 @@ __global__ void __launch_bounds__(BNT) k_batched(BatchDesc* desc, const int* ord
         c.b = d.b;
         c.q = q;
         c.prec = prec;
+        c.tile = d.tile;
         c.seed = d.seed;
         c.U = d.U;
         c.T = d.T;
         c.V = d.V;
         c.s = s;
         c.status = &d.status;
-        b_factor_one(c, d.A, d.lda, sm);
+        b_factor_one<NT>(c, d.A, d.lda, sm);
         __syncthreads();
     }
 }
@@ -608,36 +657,55 @@ __global__ void k_batched_reset(BatchDesc* desc, int count, unsigned* next) {
 
 struct TuneRow {
     int64_t nmin, nmax;
-    int tall, b;
+    int tall, b, tile;
 };
 
-std::vector<TuneRow> parse_table(const char* text) {
+struct TuneTable {
     std::vector<TuneRow> rows;
+    int threads = 256;  // threads per CTA, i.e. per matrix in flight
+};
+
+// Lines "nmin nmax tall b [tile]" (tile 32 or 64, default 64) and an
+// optional line "threads NT" (128 or 256, default 256).
+TuneTable parse_table(const char* text) {
+    TuneTable t;
     if (!text) {  // built-in defaults (randutv_batched_autotune measures replacements)
-        rows.push_back({0, 63, -1, 16});
-        rows.push_back({64, 191, -1, 32});
-        rows.push_back({192, 1LL << 40, -1, 64});
-        return rows;
+        t.rows.push_back({0, 63, -1, 16, 32});
+        t.rows.push_back({64, 191, -1, 32, 64});
+        t.rows.push_back({192, 1LL << 40, -1, 64, 64});
+        return t;
     }
-    const char* p = text;
-    while (*p) {
-        long long a, bmax;
-        int tall, b, used = 0;
-        if (sscanf(p, "%lld %lld %d %d%n", &a, &bmax, &tall, &b, &used) == 4) {
-            rows.push_back({a, bmax, tall, b});
-            p += used;
-        } else {
-            ++p;
+    std::string all(text);
+    size_t pos = 0;
+    while (pos < all.size()) {
+        size_t e = all.find('\n', pos);
+        if (e == std::string::npos) e = all.size();
+        const std::string line = all.substr(pos, e - pos);
+        pos = e + 1;
+        int nt = 0;
+        if (sscanf(line.c_str(), " threads %d", &nt) == 1) {
+            t.threads = (nt == 128) ? 128 : 256;
+            continue;
         }
+        long long a, bmax;
+        int tall, b, tile = 64;
+        const int got = sscanf(line.c_str(), "%lld %lld %d %d %d", &a, &bmax, &tall, &b, &tile);
+        if (got >= 4) t.rows.push_back({a, bmax, tall, b, (got == 5 && tile == 32) ? 32 : 64});
     }
-    return rows;
+    return t;
 }
 
-int pick_b(const std::vector<TuneRow>& rows, int64_t m, int64_t n) {
+// Block size and GEMM tile of an m x n matrix from the table.
+void pick(const TuneTable& t, int64_t m, int64_t n, int* b, int* tile) {
     int tall = m > n ? 1 : 0;
-    for (const TuneRow& r : rows)
-        if (n >= r.nmin && n <= r.nmax && (r.tall < 0 || r.tall == tall)) return std::min(std::max(r.b, 1), BMAX);
-    return 32;
+    for (const TuneRow& r : t.rows)
+        if (n >= r.nmin && n <= r.nmax && (r.tall < 0 || r.tall == tall)) {
+            *b = std::min(std::max(r.b, 1), BMAX);
+            *tile = r.tile;
+            return;
+        }
+    *b = 32;
+    *tile = 64;
 }
 
 }  // namespace
@@ -650,7 +718,7 @@ using namespace rutv;
 // workspace slot per CTA, and a CUDA graph (status reset + persistent kernel)
 // that every run replays.
 struct randutv_batch_plan {
-    int count = 0, q = 0, prec = 0, grid = 0, dev = 0;
+    int count = 0, q = 0, prec = 0, grid = 0, dev = 0, threads = 256;
     void* buf = nullptr;
     BatchDesc* ddesc = nullptr;
     int* host_status = nullptr;
@@ -663,7 +731,7 @@ namespace {
 
 randutv_status plan_build(int count, const int64_t* m, const int64_t* n, const double* const* A, const int64_t* lda,
                           double* const* U, double* const* T, double* const* V, const uint64_t* seed, int q, int prec,
-                          const int* bsel, cudaStream_t st, randutv_batch_plan** out) {
+                          const int* bsel, const int* tsel, int threads, cudaStream_t st, randutv_batch_plan** out) {
     *out = nullptr;
     if (count <= 0 || q < 0) return RANDUTV_EINVAL;
     if (prec != RANDUTV_FP64 && prec != RANDUTV_SKETCH_FP32) return RANDUTV_ENOTIMPL;
@@ -671,6 +739,7 @@ randutv_status plan_build(int count, const int64_t* m, const int64_t* n, const d
     P->count = count;
     P->q = q;
     P->prec = prec;
+    P->threads = (threads == 128) ? 128 : 256;
     int64_t maxdim = 1;
     P->h.resize(count);
     std::vector<std::pair<double, int>> cost(count);
@@ -682,7 +751,7 @@ randutv_status plan_build(int count, const int64_t* m, const int64_t* n, const d
         }
         int b = std::min(std::max(bsel[i], 1), BMAX);
         P->h[i] = BatchDesc{m[i], n[i], lda[i], A[i], U ? U[i] : nullptr, T[i], V ? V[i] : nullptr,
-                            seed ? seed[i] : 0, b, 0};
+                            seed ? seed[i] : 0, b, 0, (tsel && tsel[i] == 32) ? 32 : 64};
         maxdim = std::max(maxdim, m[i]);
         cost[i] = {est_cost(m[i], n[i], b, q), i};
     }
@@ -696,13 +765,14 @@ randutv_status plan_build(int count, const int64_t* m, const int64_t* n, const d
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->dev);
     const size_t shm = sizeof(BSmem);
-    if (cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
+    const void* kfn = (P->threads == 128) ? (const void*)k_batched<128> : (const void*)k_batched<256>;
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
         delete P;
         return RANDUTV_ECUDA;
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched, BNT, shm);
-    per_sm = std::max(1, std::min(per_sm, 2));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, P->threads, shm);
+    per_sm = std::max(1, std::min(per_sm, P->threads == 128 ? 4 : 2));
     P->grid = std::min(count, sms * per_sm);
     const int64_t L = maxdim * BMAX;
     const size_t slot_doubles = (size_t)7 * L + BMAX + 4 * (size_t)BMAX * BMAX + BMAX + (size_t)L + 64;
@@ -732,7 +802,12 @@ randutv_status plan_build(int count, const int64_t* m, const int64_t* n, const d
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
         k_batched_reset<<<std::max(1, std::min(64, (count + 255) / 256)), 256, 0, cs>>>(P->ddesc, count, next);
-        k_batched<<<P->grid, BNT, shm, cs>>>(P->ddesc, dorder, count, q, prec, slots, slot_doubles, maxdim, next);
+        if (P->threads == 128)
+            k_batched<128><<<P->grid, 128, shm, cs>>>(P->ddesc, dorder, count, q, prec, slots, slot_doubles, maxdim,
+                                                      next);
+        else
+            k_batched<256><<<P->grid, 256, shm, cs>>>(P->ddesc, dorder, count, q, prec, slots, slot_doubles, maxdim,
+                                                      next);
         ok = cudaStreamEndCapture(cs, &P->graph) == cudaSuccess;
     }
     cudaStreamDestroy(cs);
@@ -789,10 +864,11 @@ randutv_status randutv_batched_plan_create(int count, const int64_t* m, const in
     if (!plan) return RANDUTV_EINVAL;
     *plan = nullptr;
     if (count <= 0 || !m || !n || !A || !lda || !T) return RANDUTV_EINVAL;
-    std::vector<TuneRow> rows = parse_table(autotune_table);
-    std::vector<int> bsel(count);
-    for (int i = 0; i < count; ++i) bsel[i] = pick_b(rows, m[i], n[i]);
-    return plan_build(count, m, n, A, lda, U, T, V, seed, q, prec, bsel.data(), nullptr, plan);
+    const TuneTable tab = parse_table(autotune_table);
+    std::vector<int> bsel(count), tsel(count);
+    for (int i = 0; i < count; ++i) pick(tab, m[i], n[i], &bsel[i], &tsel[i]);
+    return plan_build(count, m, n, A, lda, U, T, V, seed, q, prec, bsel.data(), tsel.data(), tab.threads, nullptr,
+                      plan);
 }
 
 randutv_status randutv_batched_plan_run(randutv_batch_plan* plan, int* status, void* stream) {
@@ -829,44 +905,87 @@ randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64
                                         const uint64_t* seed, int q, int prec, char* table_out, size_t table_bytes,
                                         void* stream) {
     if (count <= 0 || !m || !n || !A || !lda || !T || !table_out || table_bytes < 64) return RANDUTV_EINVAL;
-    std::string out;
-    const int cands[3] = {16, 32, 64};
+    cudaStream_t st = (cudaStream_t)stream;
+    // times one plan over the members idx of the batch with per-member b and tile
+    auto time_plan = [&](const std::vector<int>& idx, const std::vector<int>& bs, const std::vector<int>& ts,
+                         int threads, float* ms) -> randutv_status {
+        const size_t k = idx.size();
+        std::vector<int64_t> sm_(k), sn(k), sl(k);
+        std::vector<const double*> sA(k);
+        std::vector<double*> sU(k), sT(k), sV(k);
+        std::vector<uint64_t> ss(k);
+        for (size_t t = 0; t < k; ++t) {
+            const int i = idx[t];
+            sm_[t] = m[i]; sn[t] = n[i]; sl[t] = lda[i]; sA[t] = A[i];
+            sU[t] = U ? U[i] : nullptr; sT[t] = T[i]; sV[t] = V ? V[i] : nullptr; ss[t] = seed ? seed[i] : 0;
+        }
+        randutv_batch_plan* P = nullptr;
+        randutv_status r = plan_build((int)k, sm_.data(), sn.data(), sA.data(), sl.data(), U ? sU.data() : nullptr,
+                                      sT.data(), V ? sV.data() : nullptr, ss.data(), q, prec, bs.data(), ts.data(),
+                                      threads, st, &P);
+        if (r != RANDUTV_OK) return r;
+        r = plan_run(P, nullptr, st, ms);
+        randutv_batched_plan_destroy(P);
+        return (r == RANDUTV_ENOCONV) ? RANDUTV_OK : r;
+    };
+    struct Choice {
+        int64_t lo;
+        int tall, b, tile;
+    };
+    std::vector<Choice> chosen;
+    std::vector<int> bsel(count, 32), tsel(count, 64);
+    const int bcands[3] = {16, 32, 64};
+    const int tcands[2] = {32, 64};
+    // per size class (n in [lo, 2 lo), square and tall apart): block size and GEMM tile
     for (int64_t lo = 1; lo <= (1LL << 20); lo <<= 1)
         for (int tall = 0; tall < 2; ++tall) {
             std::vector<int> idx;
             for (int i = 0; i < count; ++i)
                 if (n[i] >= lo && n[i] <= 2 * lo - 1 && ((m[i] > n[i]) ? 1 : 0) == tall) idx.push_back(i);
             if (idx.empty()) continue;
+            std::vector<int> all = idx;
             if (idx.size() > 608) idx.resize(608);  // a representative sample of the class
-            const size_t k = idx.size();
-            std::vector<int64_t> sm_(k), sn(k), sl(k);
-            std::vector<const double*> sA(k);
-            std::vector<double*> sU(k), sT(k), sV(k);
-            std::vector<uint64_t> ss(k);
-            for (size_t t = 0; t < k; ++t) {
-                int i = idx[t];
-                sm_[t] = m[i]; sn[t] = n[i]; sl[t] = lda[i]; sA[t] = A[i];
-                sU[t] = U ? U[i] : nullptr; sT[t] = T[i]; sV[t] = V ? V[i] : nullptr; ss[t] = seed ? seed[i] : 0;
+            Choice best{lo, tall, 32, 64};
+            float best_ms = 1e30f;
+            for (int b : bcands)
+                for (int tile : tcands) {
+                    float ms = 0.f;
+                    randutv_status r = time_plan(idx, std::vector<int>(idx.size(), b),
+                                                 std::vector<int>(idx.size(), tile), 256, &ms);
+                    if (r != RANDUTV_OK) return r;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = Choice{lo, tall, b, tile};
+                    }
+                }
+            chosen.push_back(best);
+            for (int i : all) {
+                bsel[i] = best.b;
+                tsel[i] = best.tile;
             }
-            int best_b = 32;
-            float best = 1e30f;
-            for (int b : cands) {
-                std::vector<int> bs(k, b);
-                randutv_batch_plan* P = nullptr;
-                randutv_status r = plan_build((int)k, sm_.data(), sn.data(), sA.data(), sl.data(),
-                                              U ? sU.data() : nullptr, sT.data(), V ? sV.data() : nullptr, ss.data(),
-                                              q, prec, bs.data(), (cudaStream_t)stream, &P);
-                if (r != RANDUTV_OK) return r;
-                float ms = 0.f;
-                r = plan_run(P, nullptr, (cudaStream_t)stream, &ms);
-                randutv_batched_plan_destroy(P);
-                if (r != RANDUTV_OK && r != RANDUTV_ENOCONV) return r;
-                if (ms < best) { best = ms; best_b = b; }
-            }
-            char line[96];
-            snprintf(line, sizeof(line), "%lld %lld %d %d\n", (long long)lo, (long long)(2 * lo - 1), tall, best_b);
-            out += line;
         }
+    // threads per matrix: the whole batch with its chosen block sizes and tiles
+    std::vector<int> every(count);
+    for (int i = 0; i < count; ++i) every[i] = i;
+    int best_threads = 256;
+    float best_ms = 1e30f;
+    for (int threads : {128, 256}) {
+        float ms = 0.f;
+        randutv_status r = time_plan(every, bsel, tsel, threads, &ms);
+        if (r != RANDUTV_OK) return r;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_threads = threads;
+        }
+    }
+    std::string out;
+    for (const Choice& ch : chosen) {
+        char line[96];
+        snprintf(line, sizeof(line), "%lld %lld %d %d %d\n", (long long)ch.lo, (long long)(2 * ch.lo - 1), ch.tall,
+                 ch.b, ch.tile);
+        out += line;
+    }
+    out += "threads " + std::to_string(best_threads) + "\n";
     if (out.size() + 1 > table_bytes) return RANDUTV_ENOMEM;
     memcpy(table_out, out.c_str(), out.size() + 1);
     return RANDUTV_OK;

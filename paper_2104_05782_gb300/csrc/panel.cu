@@ -291,17 +291,22 @@ __global__ void k_tfactor(const double* __restrict__ gram, const double* __restr
 // (W^T W)(i, k) Tf(k, j) to its running sum for every row i < k, and
 // Tf(k-1, j) = -tau_{k-1} sum(k-1) is then complete.  Every step is one FMA
 // per lane and a warp-level exchange, so the w-long dependent chain costs
-// about w short steps instead of w dot products; the block's triangle of
-// the Gram matrix is staged in shared memory (w <= 128), packed: column k
-// (rows 0..k-1) at offset k (k - 1) / 2.
-constexpr int TF_MAXW = 128;
+// about w short steps instead of w dot products.  STAGED: the block's
+// triangle of the Gram matrix is staged in shared memory (w <= 128), packed:
+// column k (rows 0..k-1) at offset k (k - 1) / 2; otherwise (w <= 256) it is
+// read from the L2-resident Gram matrix itself.
+constexpr int TF_MAXW = 256;
+constexpr int TF_STAGEW = 128;
+template <bool STAGED>
 __global__ void __launch_bounds__(32) k_tfactor_col(const double* __restrict__ gram, const double* __restrict__ tau,
                                                     int w, double* __restrict__ Tf, int* status) {
     extern __shared__ double gs[];
     __shared__ double acc[TF_MAXW];
     const int j = blockIdx.x, lane = threadIdx.x;
-    for (int k = 1; k <= j; ++k)
-        for (int i = lane; i < k; i += 32) gs[k * (k - 1) / 2 + i] = gram[i + (size_t)k * w];
+    auto G = [&](int i, int k) -> double { return STAGED ? gs[k * (k - 1) / 2 + i] : __ldg(gram + i + (size_t)k * w); };
+    if (STAGED)
+        for (int k = 1; k <= j; ++k)
+            for (int i = lane; i < k; i += 32) gs[k * (k - 1) / 2 + i] = gram[i + (size_t)k * w];
     for (int i = lane; i < j; i += 32) acc[i] = 0.0;
     double* x = Tf + (size_t)j * w;
     for (int i = j + 1 + lane; i < w; i += 32) x[i] = 0.0;
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(32) k_tfactor_col(const double* __restrict__ g
     __syncwarp();
     double xk = tj;
     for (int k = j; k >= 1; --k) {
-        for (int i = lane; i < k; i += 32) acc[i] = fma(gs[k * (k - 1) / 2 + i], xk, acc[i]);
+        for (int i = lane; i < k; i += 32) acc[i] = fma(G(i, k), xk, acc[i]);
         __syncwarp();
         xk = -tau[k - 1] * acc[k - 1];
         if (lane == 0) x[k - 1] = xk;
@@ -383,15 +388,21 @@ cudaError_t tfactor(const double* gram, const double* tau, int w, double* Tf, in
         if (e != cudaSuccess) return e;
         configured = shm;
     }
-    if (w <= TF_MAXW) {
+    if (w <= TF_STAGEW) {
         const size_t tri = sizeof(double) * (size_t)w * (w - 1) / 2;
         static thread_local size_t configured_col = 0;
         if (tri > 48 * 1024 && tri > configured_col) {
-            cudaError_t e = cudaFuncSetAttribute(k_tfactor_col, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri);
+            cudaError_t e =
+                cudaFuncSetAttribute(k_tfactor_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri);
             if (e != cudaSuccess) return e;
             configured_col = tri;
         }
-        k_tfactor_col<<<w, 32, tri, st>>>(gram, tau, w, Tf, status);
+        k_tfactor_col<true><<<w, 32, tri, st>>>(gram, tau, w, Tf, status);
+        trace_count(1);
+        return cudaGetLastError();
+    }
+    if (w <= TF_MAXW) {
+        k_tfactor_col<false><<<w, 32, 0, st>>>(gram, tau, w, Tf, status);
         trace_count(1);
         return cudaGetLastError();
     }

@@ -238,33 +238,67 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol32(const float* __restrict
     }
 }
 
-// X := X R^-1 (R upper b x b) by forward substitution, one row per thread,
-// with R packed in shared memory and four partial sums per entry (a shorter
-// dependent chain); optionally also writes the 16-bit K-major operand
-// Xb[j*ldb + r].
-__global__ void __launch_bounds__(128) k_trsm32(float* __restrict__ X, int L, int b, const float* __restrict__ R,
-                                                uint16_t* __restrict__ Xb, int64_t ldb, bool f16, DevGate gate) {
+// X := X R^-1 (R upper b x b) for 32 rows per block: the rows' tile of X
+// and the packed R sit in shared memory.  Columns go in blocks of 32: all
+// threads first subtract the already solved blocks to the left
+// (X_j -= X_{<j} R_{<j, j}, independent dot products), then one warp solves
+// the 32 x 32 triangular block, a lane per row.  Optionally also writes the
+// 16-bit K-major operand Xb[j*ldb + r].
+constexpr int TRSM_ROWS = 32;
+constexpr int TRSM_THREADS = 256;
+constexpr int TRSM_LDX = TRSM_ROWS + 1;  // tile stride: lanes of a warp hit distinct banks
+__global__ void __launch_bounds__(TRSM_THREADS) k_trsm32(float* __restrict__ X, int L, int b,
+                                                         const float* __restrict__ R, uint16_t* __restrict__ Xb,
+                                                         int64_t ldb, bool f16, DevGate gate) {
     if (gate_closed(gate)) return;
-    extern __shared__ float rs[];
-    for (int c = threadIdx.x; c < b; c += blockDim.x)
-        for (int p = 0; p <= c; ++p) rs[tri(p, c)] = R[p + (size_t)c * b];
+    extern __shared__ float tsm[];
+    float* rs = tsm;                                // packed upper triangle of R
+    float* xt = tsm + (size_t)b * (b + 1) / 2;      // TRSM_ROWS x b tile, column stride TRSM_LDX
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r0 = blockIdx.x * TRSM_ROWS;
+    const int nr = min(TRSM_ROWS, L - r0);
+    for (int c = warp; c < b; c += TRSM_THREADS / 32)
+        for (int p = lane; p <= c; p += 32) rs[tri(p, c)] = R[p + (size_t)c * b];
+    for (int e = tid; e < TRSM_ROWS * b; e += TRSM_THREADS) {
+        const int r = e % TRSM_ROWS, c = e / TRSM_ROWS;
+        xt[r + TRSM_LDX * c] = (r < nr) ? X[(r0 + r) + (int64_t)c * L] : 0.0f;
+    }
     __syncthreads();
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= L) return;
-    for (int j = 0; j < b; ++j) {
-        const float* rc = rs + tri(0, j);
-        float s0 = X[r + (int64_t)j * L], s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-        int k = 0;
-        for (; k + 3 < j; k += 4) {
-            s0 = fmaf(-X[r + (int64_t)k * L], rc[k], s0);
-            s1 = fmaf(-X[r + (int64_t)(k + 1) * L], rc[k + 1], s1);
-            s2 = fmaf(-X[r + (int64_t)(k + 2) * L], rc[k + 2], s2);
-            s3 = fmaf(-X[r + (int64_t)(k + 3) * L], rc[k + 3], s3);
+    for (int jb = 0; jb < b; jb += 32) {
+        const int wb = min(32, b - jb);
+        if (jb > 0) {  // thread (r, q) updates columns jb + q + 8u of row r
+            const int r = tid % TRSM_ROWS, q = tid / TRSM_ROWS;
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int k = 0; k < jb; ++k) {
+                const float xk = xt[r + TRSM_LDX * k];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = jb + q + 8 * u;
+                    if (j < jb + wb) acc[u] = fmaf(xk, rs[tri(k, j)], acc[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = jb + q + 8 * u;
+                if (j < jb + wb) xt[r + TRSM_LDX * j] -= acc[u];
+            }
         }
-        for (; k < j; ++k) s0 = fmaf(-X[r + (int64_t)k * L], rc[k], s0);
-        const float s = ((s0 + s1) + (s2 + s3)) / rc[j];
-        X[r + (int64_t)j * L] = s;
-        if (Xb) Xb[(int64_t)j * ldb + r] = to16(s, f16);
+        __syncthreads();
+        if (warp == 0) {
+            for (int j = jb; j < jb + wb; ++j) {
+                float s = xt[lane + TRSM_LDX * j];
+                for (int k = jb; k < j; ++k) s = fmaf(-xt[lane + TRSM_LDX * k], rs[tri(k, j)], s);
+                xt[lane + TRSM_LDX * j] = s / rs[tri(j, j)];
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < TRSM_ROWS * b; e += TRSM_THREADS) {
+        const int r = e % TRSM_ROWS, c = e / TRSM_ROWS;
+        if (r >= nr) continue;
+        const float v = xt[r + TRSM_LDX * c];
+        X[(r0 + r) + (int64_t)c * L] = v;
+        if (Xb) Xb[(int64_t)c * ldb + r0 + r] = to16(v, f16);
     }
 }
 
@@ -328,6 +362,7 @@ cudaError_t cholqr32(float* X, int64_t L, int b, int passes, uint16_t* Xb, int64
     float* G = scratch + (size_t)sms * b * b;
     float* R = G + (size_t)b * b;
     const size_t shm_tri = sizeof(float) * (size_t)b * (b + 1) / 2;
+    const size_t shm_trsm = shm_tri + sizeof(float) * (size_t)TRSM_LDX * b;
     const size_t shm_gram = sizeof(float) * 32 * (size_t)b;
     static bool configured = false;
     if (!configured) {
@@ -335,7 +370,8 @@ cudaError_t cholqr32(float* X, int64_t L, int b, int passes, uint16_t* Xb, int64
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_chol32, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 257 / 2 * 4);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_trsm32, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * 257 / 2 * 4);
+            e = cudaFuncSetAttribute(k_trsm32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (256 * 257 / 2 + TRSM_LDX * 256) * 4);
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -352,8 +388,8 @@ cudaError_t cholqr32(float* X, int64_t L, int b, int passes, uint16_t* Xb, int64
         }
         {
             TraceScope ts("cholqr_trsm", (double)L * b * b, 8.0 * (double)L * b, st);
-            k_trsm32<<<(unsigned)cdiv(L, 128), 128, shm_tri, st>>>(X, (int)L, b, R, p == passes - 1 ? Xb : nullptr,
-                                                                     ldb, f16, gate);
+            k_trsm32<<<(unsigned)cdiv(L, TRSM_ROWS), TRSM_THREADS, shm_trsm, st>>>(
+                X, (int)L, b, R, p == passes - 1 ? Xb : nullptr, ldb, f16, gate);
         }
         trace_count(4);
         cudaError_t e = cudaGetLastError();

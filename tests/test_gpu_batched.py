@@ -152,8 +152,10 @@ def test_batched_autotune_table(rutv):
     r, table = rutv.randutv_batched_autotune([M.shape[0] for M in mats], [M.shape[1] for M in mats], A,
                                              [M.shape[0] for M in mats], None, T, None, [0, 1, 2], 1)
     assert r == 0
-    rows = [list(map(int, line.split())) for line in table.strip().splitlines()]
-    assert len(rows) == 3 and all(row[3] in (16, 32, 64) for row in rows)
+    lines = table.strip().splitlines()
+    assert lines[-1] in ("threads 128", "threads 256")
+    rows = [list(map(int, line.split())) for line in lines[:-1]]
+    assert len(rows) == 3 and all(row[3] in (16, 32, 64) and row[4] in (32, 64) for row in rows)
     # the table drives a run
     r2, status, _, T2, _ = run_batch(rutv, mats, 0, 1, table=table, want_uv=False)
     assert r2 == 0
@@ -201,8 +203,10 @@ def test_batched_autotuned_workload_slice_matches_oracle(rutv):
     r, table = rutv.randutv_batched_autotune([M.shape[0] for M in mats], [M.shape[1] for M in mats], A,
                                              [M.shape[0] for M in mats], None, T0, None, seeds, 2)
     assert r == 0
-    rows = [tuple(map(int, line.split())) for line in table.strip().splitlines()]
-    assert rows and all(row[3] in (16, 32, 64) for row in rows)
+    lines = table.strip().splitlines()
+    assert lines[-1].startswith("threads ")
+    rows = [tuple(map(int, line.split())) for line in lines[:-1]]
+    assert rows and all(row[3] in (16, 32, 64) and row[4] in (32, 64) for row in rows)
 
     def b_of(k):
         m, n = mats[k].shape
@@ -214,3 +218,16 @@ def test_batched_autotuned_workload_slice_matches_oracle(rutv):
     r, status, U, T, V = run_batch(rutv, mats, 0, 2, seeds=seeds, table=table)
     assert r == rutv.RANDUTV_OK and all(s == 0 for s in status)
     _check_against_oracle(mats, b_of, 2, U, T, V, seeds)
+
+
+@pytest.mark.parametrize("threads,tile", [(128, 32), (128, 64), (256, 32), (256, 64)])
+def test_batched_threads_and_tiles_match_oracle(rutv, threads, tile):
+    """Every shape the autotuner can pick (threads per matrix, GEMM tile)
+    computes the same factorization as the oracle."""
+    shapes = [(96, 48), (130, 130), (33, 17), (200, 100), (300, 300), (70, 35)]
+    mats = make_batch(shapes, kind="normal")
+    seeds = [40 + k for k in range(len(mats))]
+    table = "0 100000 -1 32 %d\nthreads %d\n" % (tile, threads)
+    r, status, U, T, V = run_batch(rutv, mats, 0, 2, seeds=seeds, table=table)
+    assert r == rutv.RANDUTV_OK and all(s == 0 for s in status)
+    _check_against_oracle(mats, lambda k: 32, 2, U, T, V, seeds)
