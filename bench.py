@@ -245,6 +245,59 @@ def cpu_blas_sample(n: int, b: int, q: int, kind: str):
     return randutv_flops(n, n, b, q) / dt / 1e12, dt, len(os.sched_getaffinity(0))
 
 
+# The BLAS-based CPU comparison at the full size takes minutes, so it is
+# measured once (python bench.py --cpu-blas-full) and recorded here.
+CPU_BLAS_FULL_RECORD = os.path.join(ROOT, "cpu_blas_full_size.json")
+
+
+def run_cpu_blas_full(args):
+    """One blas_randutv factorization of the full-size workload on the host
+    cores; the matrix is built on the GPU with the bench's own recipe and copied
+    to the host.  Writes CPU_BLAS_FULL_RECORD and prints it."""
+    import datetime
+
+    import numpy as np
+    import torch
+
+    import oracle
+    import synthetic
+
+    n = args.n
+    m = args.m if args.m > 0 else n
+    A, _ = synthetic.test_matrix_device(m, n, args.spectrum, 1, 2, device=torch.device("cuda", 0))
+    Ah = np.asfortranarray(A.cpu().numpy())
+    del A
+    oracle.build()
+    t0 = time.perf_counter()
+    blas_randutv(Ah, args.b, args.q, 0, oracle.gaussian)
+    dt = time.perf_counter() - t0
+    rec = {"value": randutv_flops(m, n, args.b, args.q) / dt / 1e12, "unit": "TFLOP/s", "seconds": dt,
+           "cores": len(os.sched_getaffinity(0)),
+           "kind": "blocked randUTV on numpy's BLAS/LAPACK (bench.blas_randutv)",
+           "sample": "one %dx%d %s-spectrum factorization (b=%d, q=%d, U and V formed): the full workload size"
+                     % (m, n, args.spectrum, args.b, args.q),
+           "command": "python bench.py --cpu-blas-full --n %d --b %d --q %d --spectrum %s"
+                      % (n, args.b, args.q, args.spectrum),
+           "measured_utc": datetime.datetime.utcnow().strftime("%Y-%m-%dT%H:%M:%SZ")}
+    with open(CPU_BLAS_FULL_RECORD, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec), flush=True)
+
+
+def cpu_blas_full_record(m: int, n: int, b: int, q: int, spectrum: str):
+    """The recorded full-size BLAS CPU run for this workload, or None."""
+    try:
+        with open(CPU_BLAS_FULL_RECORD) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    want = "one %dx%d %s-spectrum factorization (b=%d, q=%d" % (m, n, spectrum, b, q)
+    if not rec.get("sample", "").startswith(want):
+        return None
+    rec["source"] = "recorded by a separate run of its command (minutes of CPU time), not measured in this run"
+    return rec
+
+
 def diag_quality(d, sigma, b: int) -> dict:
     """How closely |T_ii| tracks the prescribed singular values sigma_i.
 
@@ -646,6 +699,7 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "cpu_baseline_blas": cpu_blas,
+            "cpu_baseline_blas_full_size": cpu_blas_full_record(m, n, b, q, args.spectrum),
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -790,13 +844,17 @@ def main():
     p.add_argument("--count", type=int, default=4096)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-blas-full", action="store_true",
+                   help="only time the BLAS-based CPU randUTV once at the full size and record it")
     args = p.parse_args()
     if args.workload == "single" and args.prec == "fp32":
         p.error("--prec fp32 (the FP32 sketch) applies to --workload batched only")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.cpu_blas_full:
+        run_cpu_blas_full(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     elif args.workload == "batched":
         run_batched(args, rank, world, local_rank)

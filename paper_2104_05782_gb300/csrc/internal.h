@@ -115,6 +115,9 @@ int learnq_nparam();
 // compressed q = 0 sketch.
 cudaError_t learnq_features(const double* dprev, int64_t dstride, int wprev, const double* R, int64_t ldr, int w,
                             float* f, cudaStream_t st);
+// rdiag (w doubles) := |R_jj| of the Householder QR of E (e x w, ld lde) in
+// FP32 in one block; e <= 256, w <= 128.
+cudaError_t feature_rdiag(const double* E, int64_t lde, int e, int w, double* rdiag, cudaStream_t st);
 // q (device) := the network's choice; also written to *qlog when qlog != null.
 cudaError_t learnq_infer(const float* P, const float* f, int fallback, int* q, int* qlog, cudaStream_t st);
 size_t learnq_train_scratch_floats(int N);

@@ -15,7 +15,7 @@
 //              R of the q = 0 sketch Y0 = T22^T G compressed to at most 2b
 //              rows by a second Gaussian sketch (Omega Y0, Omega 2b x n'; a
 //              subspace embedding, so the decay of R is kept to a constant
-//              factor; Y0 itself when n' <= 2b).
+//              factor; Y0 itself when n' <= 2b), factored in FP32 (b <= 128).
 // Training kernels: per-sample forward, per-sample backward, gradient
 // reductions over the batch in a fixed order (deterministic, no atomics),
 // and Adam.  Cross-entropy loss averaged over the batch.
@@ -88,6 +88,73 @@ __global__ void k_learnq_features(const double* __restrict__ dprev, int64_t dstr
             float v = (d0 > 0.0 && dj > 0.0) ? (float)log10(dj / d0) : -16.0f;
             f[t] = fmaxf(v, -16.0f);
         }
+    }
+}
+
+// |R_jj| of the Householder QR of E (e x w, FP64, ld lde; e <= 256, w <= 128)
+// for the learned-q features, in FP32 in one block: E is scaled by its
+// largest entry and held in shared memory; warp 0 builds each reflector
+// (e <= 256 rows: eight per lane and a shuffle sum), then every warp applies it
+// to its share of the remaining columns.  Ratios |R_jj| / |R_00| come out to
+// FP32 accuracy and saturate near 1e-7, where the remaining columns are
+// rounding; the features clip there consistently in training and use.
+constexpr int FQR_THREADS = 1024;
+__global__ void __launch_bounds__(FQR_THREADS) k_feature_rdiag32(const double* __restrict__ E, int64_t lde, int e, int w,
+                                                                 double* __restrict__ rdiag) {
+    extern __shared__ float fa[];  // e x w, column stride ld = e + 1
+    __shared__ float s_tau, s_inv;
+    __shared__ double s_max[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ld = e + 1;
+    double mx = 0.0;
+    for (int t = tid; t < e * w; t += FQR_THREADS) mx = fmax(mx, fabs(E[(t % e) + (int64_t)(t / e) * lde]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_max[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int k = 0; k < FQR_THREADS / 32; ++k) m = fmax(m, s_max[k]);
+        s_max[0] = m;
+    }
+    __syncthreads();
+    const double scale = s_max[0] > 0.0 ? 1.0 / s_max[0] : 1.0;
+    for (int t = tid; t < e * w; t += FQR_THREADS) {
+        const int r = t % e, c = t / e;
+        fa[r + ld * c] = (float)(E[r + (int64_t)c * lde] * scale);
+    }
+    __syncthreads();
+    for (int j = 0; j < w && j < e; ++j) {
+        if (warp == 0) {  // the reflector of column j (dlarfg rule), v stored in place
+            float xi2 = 0.0f;
+            for (int r = j + 1 + lane; r < e; r += 32) xi2 = fmaf(fa[r + ld * j], fa[r + ld * j], xi2);
+            for (int o = 16; o > 0; o >>= 1) xi2 += __shfl_xor_sync(0xffffffffu, xi2, o);
+            const float alpha = fa[j + ld * j];
+            float beta = alpha, tau = 0.0f, inv = 0.0f;
+            if (xi2 > 0.0f) {
+                const float h = sqrtf(fmaf(alpha, alpha, xi2));
+                beta = (alpha >= 0.0f) ? -h : h;
+                tau = (beta - alpha) / beta;
+                inv = 1.0f / (alpha - beta);
+            }
+            for (int r = j + 1 + lane; r < e; r += 32) fa[r + ld * j] *= inv;
+            if (lane == 0) {
+                rdiag[j] = fabs((double)beta);
+                s_tau = tau;
+                s_inv = inv;
+            }
+        }
+        __syncthreads();
+        const float tau = s_tau;
+        if (tau != 0.0f)
+            for (int c = j + 1 + warp; c < w; c += FQR_THREADS / 32) {  // column c -= tau v (v^T column c)
+                float d = 0.0f;
+                for (int r = j + 1 + lane; r < e; r += 32) d = fmaf(fa[r + ld * j], fa[r + ld * c], d);
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                d = tau * (d + fa[j + ld * c]);
+                if (lane == 0) fa[j + ld * c] -= d;
+                for (int r = j + 1 + lane; r < e; r += 32) fa[r + ld * c] = fmaf(-d, fa[r + ld * j], fa[r + ld * c]);
+            }
+        __syncthreads();
     }
 }
 
@@ -230,6 +297,21 @@ __global__ void k_sum_loss(const float* __restrict__ l, int N, float* out) {
 }  // namespace
 
 int learnq_nparam() { return NPARAM; }
+
+cudaError_t feature_rdiag(const double* E, int64_t lde, int e, int w, double* rdiag, cudaStream_t st) {
+    if (e > 256 || w > 128 || e < 1 || w < 1) return cudaErrorInvalidValue;
+    const size_t shm = sizeof(float) * (size_t)(e + 1) * w;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t err = cudaFuncSetAttribute(k_feature_rdiag32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(sizeof(float) * 257 * 128));
+        if (err != cudaSuccess) return err;
+        configured = true;
+    }
+    k_feature_rdiag32<<<1, FQR_THREADS, shm, st>>>(E, lde, e, w, rdiag);
+    trace_count(1);
+    return cudaGetLastError();
+}
 
 cudaError_t learnq_features(const double* dprev, int64_t dstride, int wprev, const double* R, int64_t ldr, int w,
                             float* f, cudaStream_t st) {

@@ -11,14 +11,13 @@
 //   (op(A) op(B))(r,c) = 2^{eA_r + eB_c} sum_d 2^{-7d} sum_{s+t=d} (a_s b_t^T)(r,c).
 // With S = 8 digits (56 bits) and the digit pairs s + t <= S + 1 kept, the
 // truncation error is below 9.06 K 2^{-56} 2^{eA_r + eB_c} (the dropped pairs
-// weigh 2^{-70} each).  One tcgen05 accumulator per digit sum d lives in TMEM
-// (8 x 32 FP32 columns per 128 x 32 output tile, two buffers); every 128 of K
-// the partial sums are exact integers in FP32 (<= 8 pairs x 128 x 127^2 <
-// 2^24), and they are added, exactly, into two 64-bit integer words per
-// output element with their power-of-two weights.  The exact sum is rounded
-// once to FP64 with integer instructions, so the only FP64 instruction per
-// element is the final C + v, and the product's error is the truncation plus
-// that one rounding.
+// weigh 2^{-70} each), and the double-float fold adds at most
+// 72 ceil(K / 128) 2^{-48} sum_k |a_k b_k|.  One tcgen05 accumulator per digit sum d
+// lives in TMEM (8 x 32 FP32 columns per 128 x 32 output tile, two buffers);
+// every 128 of K the partial sums are exact integers in FP32 (<= 8 pairs x
+// 128 x 127^2 < 2^24), and they are folded into double-float (hi, lo) FP32
+// registers with exact power-of-two weights.  The final value gets one FP64
+// epilogue per element.
 //
 // Splitting works on the FP64 bit pattern with integer instructions only
 // (GB300's FP64 pipe would make a floating-point split cost more than the
@@ -86,14 +85,10 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     d |= (uint64_t)2 << 61;
     return d;
 }
-// The integer held exactly by an FP32 accumulator (|v| < 2^24), read from its
-// bit pattern with integer instructions: v = m 2^(E - 150).
-__device__ __forceinline__ int f32_exact_int(uint32_t u) {
-    const int E = (int)((u >> 23) & 0xFF);
-    const int m = (int)((u & 0x7FFFFFu) | 0x800000u);
-    const int sh = 150 - E;
-    const int a = (E == 0) ? 0 : (sh >= 0 ? (sh < 32 ? (m >> sh) : 0) : (m << (-sh)));
-    return (u >> 31) ? -a : a;
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
 }
 
 // ---------------------------------------------------------------- splitting
@@ -244,37 +239,18 @@ constexpr int OZ_ACC = OZ_S * OZ_TN;                    // 256 TMEM columns per 
 // (the barriers live in static shared memory)
 constexpr int OZ_SMEM = OZ_AST * OZ_A_BYTES + OZ_BST * OZ_B_BYTES + 1024;
 
-// (hi 2^28 + lo) 2^e2, an exact 128-bit integer times a power of two,
-// rounded once to FP64 (round to nearest, ties to even) with integer
-// instructions.  A result below the FP64 normal range is flushed to a signed
-// zero and one above it becomes a signed infinity (as FP64 arithmetic
-// overflows); neither occurs for data within a few hundred binades of 1.
-__device__ __forceinline__ double exact_to_f64(long long hi, long long lo, int e2) {
-    const __int128 N = ((__int128)hi << 28) + (__int128)lo;
-    if (N == 0) return 0.0;
-    const bool neg = N < 0;
-    unsigned __int128 a = neg ? (unsigned __int128)(-N) : (unsigned __int128)N;
-    const unsigned long long ah = (unsigned long long)(a >> 64), al = (unsigned long long)a;
-    const int nb = ah ? 128 - __clzll((long long)ah) : 64 - __clzll((long long)al);  // bit length of a
-    unsigned long long mant;
-    int ex = nb - 53;  // a = mant 2^ex after rounding to 53 bits
-    if (ex <= 0) {
-        mant = al << (-ex);
-    } else {
-        mant = (unsigned long long)(a >> ex);
-        const unsigned __int128 rem = a & (((unsigned __int128)1 << ex) - 1);
-        const unsigned __int128 half = (unsigned __int128)1 << (ex - 1);
-        if (rem > half || (rem == half && (mant & 1ull))) ++mant;
-        if (mant >> 53) {
-            mant >>= 1;
-            ++ex;
-        }
-    }
-    const int be = ex + 52 + e2 + 1023;  // biased exponent of mant 2^(ex + e2), mant in [2^52, 2^53)
-    const unsigned long long sign = (unsigned long long)neg << 63;
-    if (be <= 0) return __longlong_as_double((long long)sign);
-    if (be >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
-    return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+// FP32 value x times 2^sh, built as an FP64 bit pattern with integer
+// instructions (exact); zero and FP32 subnormals give 0; returns false when
+// the result would leave the FP64 normal range.
+__device__ __forceinline__ bool f32_to_f64_scaled(float x, int sh, double& out) {
+    const uint32_t u = __float_as_uint(x);
+    const int e8 = (int)((u >> 23) & 0xFF);
+    if (e8 == 0) { out = 0.0; return true; }
+    const int e = e8 - 127 + 1023 + sh;
+    if (e <= 0 || e >= 2047) return false;
+    out = __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | ((unsigned long long)e << 52) |
+                                           ((unsigned long long)(u & 0x7FFFFF) << 29)));
+    return true;
 }
 
 struct OzJobs {
@@ -468,16 +444,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
             const int cb = n0 + half * 16;
             const int ncols = (r < M) ? min(16, N - cb) : 0;
             const int er = (ncols > 0) ? eA[r] : INT_MIN;
+            int ec[16];
             double cv[16];
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
+            for (int c = 0; c < 16; ++c) {
+                ec[c] = (c < ncols) ? eB[cb + c] : INT_MIN;
                 cv[c] = (!partial && bmode != 0 && c < ncols) ? C[r + (int64_t)(cb + c) * ldc] : 0.0;
-            // the value is 2^(er + ec - 63) (shi 2^28 + slo), with the digit
-            // sums d = 0..3 in shi (weights 2^(7(3 - d))) and d = 4..7 in slo
-            // (weights 2^(7(7 - d))): exact integers, whatever the number of chunks
-            long long shi[16], slo[16];
+            }
+            float hi[16], lo[16];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) shi[c] = slo[c] = 0;
+            for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0.0f;
             const int nch = (nkb + OZ_CHUNK - 1) / OZ_CHUNK;
             bool ok = true;
             for (int ch = 0; ch < nch; ++ch, ++chunk) {
@@ -486,31 +462,40 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                 if (!ok || s_abort) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + buf * OZ_ACC + (uint32_t)(half * 16);
+#pragma unroll 1
+                for (int g = 1; g >= 0; --g) {  // digit sums 7..4, then 3..0: four loads, one wait
+                    uint32_t v[4][16];
 #pragma unroll
-                for (int g = 1; g >= 0; --g) {      // digit sums 7..4, then 3..0
+                    for (int i = 0; i < 4; ++i) {
+                        const uint32_t ta = tbase + (uint32_t)((4 * g + 3 - i) * OZ_TN);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+                            "%13,%14,%15}, [%16];"
+                            : "=r"(v[i][0]), "=r"(v[i][1]), "=r"(v[i][2]), "=r"(v[i][3]), "=r"(v[i][4]),
+                              "=r"(v[i][5]), "=r"(v[i][6]), "=r"(v[i][7]), "=r"(v[i][8]), "=r"(v[i][9]),
+                              "=r"(v[i][10]), "=r"(v[i][11]), "=r"(v[i][12]), "=r"(v[i][13]), "=r"(v[i][14]),
+                              "=r"(v[i][15])
+                            : "r"(ta));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {   // columns 8h .. 8h+7: four loads, one wait
-                        uint32_t v[4][8];
+                    for (int i = 0; i < 4; ++i) {
+                        const int d = 4 * g + 3 - i;
+                        const float w = __int_as_float((127 - 7 * (d + 2)) << 23);  // 2^{-7(d+2)}
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const uint32_t ta = tbase + (uint32_t)((4 * g + 3 - i) * OZ_TN + 8 * h);
-                            asm volatile(
-                                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                : "=r"(v[i][0]), "=r"(v[i][1]), "=r"(v[i][2]), "=r"(v[i][3]), "=r"(v[i][4]),
-                                  "=r"(v[i][5]), "=r"(v[i][6]), "=r"(v[i][7])
-                                : "r"(ta));
-                        }
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        // digit sum d = 4 g + 3 - i has weight 2^(7 i) in its word
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            long long t = (long long)f32_exact_int(v[0][c]);
-#pragma unroll
-                            for (int i = 1; i < 4; ++i) t += (long long)f32_exact_int(v[i][c]) << (7 * i);
-                            if (g) slo[8 * h + c] += t;
-                            else shi[8 * h + c] += t;
+                        for (int c = 0; c < 16; ++c) {
+                            float s, e;
+                            two_sum(hi[c], __uint_as_float(v[i][c]) * w, s, e);
+                            hi[c] = s;
+                            lo[c] += e;
                         }
                     }
+                }
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {  // renormalise (fast two-sum)
+                    float s = hi[c] + lo[c];
+                    lo[c] = lo[c] - (s - hi[c]);
+                    hi[c] = s;
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
@@ -529,11 +514,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                 for (int c = 0; c < 16; ++c) {
                     if (c >= ncols) continue;
                     double v = 0.0;
-                    const int ecc = eB[cb + c];
-                    if (er != INT_MIN && ecc != INT_MIN) {
-                        v = exact_to_f64(shi[c], slo[c], er + ecc - 63);
-                        if (amode == 0) v *= alpha;
-                        else v = __longlong_as_double(__double_as_longlong(v) ^ sgn);
+                    if (er != INT_MIN && ec[c] != INT_MIN) {
+                        double dh, dl;
+                        if (amode != 0 && f32_to_f64_scaled(hi[c], er + ec[c], dh) &&
+                            f32_to_f64_scaled(lo[c], er + ec[c], dl)) {
+                            v = __longlong_as_double(__double_as_longlong(dh) ^ sgn) +
+                                __longlong_as_double(__double_as_longlong(dl) ^ sgn);
+                        } else {  // general alpha or extreme exponents
+                            const double scale = ldexp(alpha, er + ec[c]);
+                            v = fma((double)hi[c], scale, (double)lo[c] * scale);
+                        }
                     }
                     if (partial) {
                         Pz[r + (size_t)(cb + c) * M] = v;

@@ -72,6 +72,7 @@ struct Workspace {
     int* qdev;        // chosen q
     double* dq;       // candidate diagonals, 4 x w (trace mode)
     double* rdiag;    // learned q / trace: the R diagonal of the last panel QR (w)
+    double* sdiag;    // learned q / trace: |R_jj| of the compressed sketch (w)
     float* qmodel;    // network parameters on the device
     void* oz;         // digit slices and exponents of the emulated FP64 products
     size_t oz_bytes;
@@ -177,7 +178,7 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec, bool qr_first
         lp ? sizeof(float) * (size_t)mx * npad : 0,                 // Y / Z in FP32
         lp ? sizeof(float) * cholqr_scratch_floats((int)npad, sms) : 0,
         lp ? sizeof(unsigned long long) : 0,                        // max |T22|
-        sizeof(float) * 32 + sizeof(double) * 5 * (size_t)wmax,     // learned-q features, q, candidates, R diagonal
+        sizeof(float) * 32 + sizeof(double) * 6 * (size_t)wmax,     // learned-q features, q, candidates, R diagonals
         sizeof(float) * (size_t)learnq_nparam(),                    // learned-q model
         emulated_prec(prec) ? oz_work_bytes(mx, std::max<int64_t>(wmax, 128), mx) : 0,   // Ozaki digits
         emulated_prec(prec) ? oz_operand_bytes(m, n) : 0,                               // T(:, k0:n) by rows
@@ -234,6 +235,7 @@ Workspace carve(void* base, const Layout& L) {
     w.qdev = (int*)(w.feat + 16);
     w.dq = (double*)(p + L.off[26] + sizeof(float) * 32);
     w.rdiag = w.dq + 4 * (size_t)L.wmax;
+    w.sdiag = w.rdiag + (size_t)L.wmax;
     w.qmodel = (float*)(p + L.off[27]);
     w.oz = (void*)(p + L.off[28]);
     w.oz_bytes = L.off[29] - L.off[28];
@@ -952,8 +954,8 @@ constexpr int64_t kFeatureDrawStep = (int64_t)1 << 40;
 
 // Features of block step i (needs Y0 = T22^T G in c.w.Y): the Householder R
 // of E = Omega Y0 (2b x b, two Gaussian draws Omega_1, Omega_2 of b rows each;
-// E = Y0 when n' <= 2b) and the previous block's R diagonal (from its panel
-// QR), read from dprev[j * dstride].
+// E = Y0 when n' <= 2b), in FP32 in one block for b <= 128, and the previous
+// block's R diagonal (from its panel QR), read from dprev[j * dstride].
 cudaError_t block_features(Ctx& c, int64_t i, int64_t np, const double* dprev, int64_t dstride) {
     const int b = c.b;
     TraceScope ts("learnq_features", 4.0 * (double)np * b * b, 16.0 * (double)np * b, c.st);
@@ -966,6 +968,10 @@ cudaError_t block_features(Ctx& c, int64_t i, int64_t np, const double* dprev, i
             CK(gaussian_f64(c.seed, kFeatureDrawStep + 2 * i + h, np, b, c.w.Z, np, c.st));
             CK(gemm(c, "learnq_features", true, false, b, b, np, 1.0, c.w.Z, np, c.w.Y, np, 0.0, E + h * b, e));
         }
+    }
+    if (e <= 256 && b <= 128) {  // |R_jj| of E by a one-block FP32 QR
+        CK(feature_rdiag(E, e, e, b, c.w.sdiag, c.st));
+        return learnq_features(dprev, dstride, dprev ? b : 0, c.w.sdiag, 0, b, c.w.feat, c.st);
     }
     CK(panel_qr(E, e, e, b, c.w.tau, c.w.pscr, c.w.bars, c.w.status, panel_sms(c), c.st));
     return learnq_features(dprev, dstride, dprev ? b : 0, E, e, b, c.w.feat, c.st);

@@ -82,6 +82,7 @@ def check_utv(A, U, T, V, triangular=True):
     (97, 1, 16, 1, "normal", 5),             # one column
     (64, 64, 1, 1, "normal", 4),             # b = 1
     (200, 150, 17, 3, "geometric10", 9),     # odd b (Jacobi padding), q = 3
+    (600, 520, 200, 1, "normal", 6),         # b > 128: the wide T factor, cluster Jacobi without preconditioning
 ])
 def test_parity_against_oracle(rutv, m, n, b, q, kind, seed):
     A = synthetic.test_matrix(m, n, kind, 10 + seed, 20 + seed)

@@ -8,10 +8,9 @@ integers, step by step:
 - row and column scales from the largest exponent;
 - 8 signed digits of 7 bits each;
 - the 36 digit pairs with s + t <= 7 (0-based);
-- exact integer digit sums over chunks of 128 (each below 2^24, so FP32
-  accumulators hold them exactly);
-- their exact sum with power-of-two weights, held in integers;
-- one rounding of that exact sum to FP64.
+- exact integer digit sums over chunks of 128;
+- a double-float FP32 fold of each chunk;
+- the FP64 result.
 
 It then checks the error bound stated for the scheme. It does not import or
 run the CUDA code. It pins the design's arithmetic and error model; the GPU
@@ -52,24 +51,32 @@ def digits(X, e):
                      for s in range(S)])
 
 
-def emulated_dot(da, db, er, ec):
-    """One output element from the digits of a row (da[s, k]) and a column (db[t, k]).
+def f32(x):
+    return np.float32(x)
 
-    Each chunk's digit sums are exact integers; digit sum d weighs
-    2^(-7(d+2)) = 2^-63 2^(49-7d), so sum_d sums[d] 2^(49-7d) is an exact
-    integer N, accumulated over all chunks, and the result is N 2^(er+ec-63)
-    rounded once to FP64."""
+
+def emulated_dot(da, db, er, ec):
+    """One output element from the digits of a row (da[s, k]) and a column (db[t, k])."""
     if er == NO_SCALE or ec == NO_SCALE:
         return 0.0, 0
     K = da.shape[1]
-    N = 0
+    hi, lo = f32(0.0), f32(0.0)
     max_sum = 0
     for k0 in range(0, K, CHUNK):
         sl = slice(k0, min(K, k0 + CHUNK))
         sums = [sum(int(np.dot(da[s, sl], db[d - s, sl])) for s in range(d + 1)) for d in range(S)]
         max_sum = max(max_sum, max(abs(x) for x in sums))
-        N += sum(sums[d] << (49 - W * d) for d in range(S))
-    return float(Fraction(N) * Fraction(2) ** int(er + ec - 63)), max_sum
+        for d in range(S - 1, -1, -1):      # fold: two-sum into hi, errors into lo
+            x = f32(f32(sums[d]) * f32(2.0 ** (-W * (d + 2))))
+            s_ = f32(hi + x)
+            bb = f32(s_ - hi)
+            err = f32(f32(hi - f32(s_ - bb)) + f32(x - bb))
+            hi, lo = s_, f32(lo + err)
+        s_ = f32(hi + lo)                  # renormalise
+        lo = f32(lo - f32(s_ - hi))
+        hi = s_
+    scale = 2.0 ** int(er + ec)
+    return float(hi) * scale + float(lo) * scale, max_sum
 
 
 def exact_dot(a, b):
@@ -81,12 +88,16 @@ def bound(a, b, er, ec):
 
     truncation of both operands and the dropped pairs (s + t >= 8):
         2^(er+ec) K (2 + 7.06) 2^-56
-    and the one rounding of the exact sum to FP64: 2^-53 |result|.
+    rounding of lo in the fold, at most 8 per chunk, each below 9 2^-48 of
+    the running sum (bounded by sum_k |a_k b_k| plus the truncation):
+        72 ceil(K / 128) 2^-48 sum_k |a_k b_k|
+    and the final FP64 addition: 2^-53 |result|.
     """
     K = len(a)
     sab = float(np.sum(np.abs(a) * np.abs(b)))
     trunc = 2.0 ** float(er + ec) * K * 9.06 * 2.0 ** -56
-    return trunc + 2.0 ** -53 * (sab + trunc)
+    fold = 72 * -(-K // CHUNK) * 2.0 ** -48 * (sab + trunc)
+    return trunc + fold + 2.0 ** -53 * (sab + trunc)
 
 
 def _cases():
@@ -118,21 +129,6 @@ def test_digits_are_bf16_exact_and_reconstruct_to_56_bits():
                 assert y == 0 or (y > 0) == (x > 0)
             else:                                              # subnormals are dropped
                 assert y == 0
-
-
-def test_integer_words_do_not_overflow():
-    """The kernel keeps each output's exact sum in two signed 64-bit words,
-    digit sums 0..3 and 4..7, each weighted 2^(7 i), i = 0..3, within its word:
-    one chunk adds less than 2^24 (1 + 2^7 + 2^14 + 2^21) < 2^46 to a word, so
-    the words hold the sum of up to 2^17 chunks (K up to 2^24) exactly."""
-    per_chunk = (2 ** 24) * (1 + 2 ** 7 + 2 ** 14 + 2 ** 21)
-    assert per_chunk < 2 ** 46 and per_chunk * 2 ** 17 < 2 ** 63
-    # the two words recombine into the same N as the model's single sum
-    rng = np.random.default_rng(4)
-    sums = [int(x) for x in rng.integers(-(2 ** 23), 2 ** 23, S)]
-    hi = sum(sums[d] << (W * (3 - d)) for d in range(4))
-    lo = sum(sums[d] << (W * (7 - d)) for d in range(4, 8))
-    assert (hi << 28) + lo == sum(sums[d] << (49 - W * d) for d in range(S))
 
 
 def test_chunk_sums_are_exact_in_fp32():
@@ -175,5 +171,5 @@ def test_typical_error_against_fp64_dot():
         sab = float(np.sum(np.abs(A[i] * B[:, i])))
         emu.append(float(abs(Fraction(v) - exact)) / sab)
         f64.append(float(abs(Fraction(float(np.dot(A[i], B[:, i]))) - exact)) / sab)
-    assert np.median(emu) <= 2.0 ** -50
-    assert np.median(emu) <= 4 * max(np.median(f64), 2.0 ** -53)
+    assert np.median(emu) <= 2.0 ** -44
+    assert np.median(emu) <= 64 * max(np.median(f64), 2.0 ** -53)
