@@ -189,8 +189,11 @@ void randutv_set_limits(int64_t wait_polls, int max_sweeps);
 /*
  * randutv_factor_host -- randutv_factor on HOST buffers: copies A to the device,
  * factors it, copies U, T, V back (U or V NULL skips that factor).  A (lda >= m),
- * U (m x m), T (m x n), V (n x n) are host pointers, column-major; page-locked
- * (pinned) host memory avoids a staging copy.  The device copies of A/T, U
+ * U (m x m), T (m x n), V (n x n) are host pointers, column-major.  Page-locked
+ * (pinned) host buffers are read and written by the library's own copy
+ * kernels through their device addresses (these keep the host link's full
+ * rate, where DMA copies were measured an order of magnitude slower after
+ * the link had been idle); other host memory goes through cudaMemcpy.  The device copies of A/T, U
  * and V live in buffers the library caches per device and grows as needed
  * (like the workspace), so repeated calls do not allocate; calls on one device
  * must therefore not overlap (from several host threads).  Synchronous.

@@ -82,6 +82,9 @@ cudaError_t copy_matrix(const double* src, int64_t lds, double* dst, int64_t ldd
 // Block column T(k0:m, k0:k0+w) := [diag(D); 0].
 cudaError_t set_diag_block(double* T, int64_t ldt, int64_t k0, int64_t m, int w, const double* D,
                            cudaStream_t st);
+// dst[0:count) := src[0:count) by the SMs (either may be pinned host memory
+// given by its device address).
+cudaError_t copy_flat(const double* src, double* dst, int64_t count, int sms, cudaStream_t st);
 // X(i, j) := 0 for i > j (rows x cols).
 cudaError_t zero_below_diag(double* X, int64_t ld, int64_t rows, int64_t cols, cudaStream_t st);
 // X (m x m) := diag(X(0:n, 0:n), I_{m-n}).

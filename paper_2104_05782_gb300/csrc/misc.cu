@@ -99,6 +99,19 @@ __global__ void k_embed_identity(double* __restrict__ X, int64_t ld, int64_t m, 
     }
 }
 
+// Flat copies by the SMs (dst, src 16- or 8-byte aligned): used between
+// pinned host memory and the device, where they keep the link's full rate
+// even after it has been idle (DMA copies were measured an order of
+// magnitude slower then).
+__global__ void k_copy16(const double2* __restrict__ src, double2* __restrict__ dst, int64_t n2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+__global__ void k_copy8(const double* __restrict__ src, double* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
 unsigned grid_for(int64_t total) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), 8192)); }
 
 }  // namespace
@@ -137,6 +150,20 @@ cudaError_t set_diag_block(double* T, int64_t ldt, int64_t k0, int64_t m, int w,
                            cudaStream_t st) {
     if (w <= 0 || m - k0 <= 0) return cudaSuccess;
     k_set_diag_block<<<grid_for((m - k0) * w), 256, 0, st>>>(T, ldt, k0, m, w, D);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
+cudaError_t copy_flat(const double* src, double* dst, int64_t count, int sms, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::max(1, 4 * sms);
+    if (((uintptr_t)src | (uintptr_t)dst) % 16 == 0) {
+        const int64_t n2 = count / 2;
+        if (n2 > 0) k_copy16<<<blocks, 512, 0, st>>>((const double2*)src, (double2*)dst, n2);
+        if (count % 2) k_copy8<<<1, 32, 0, st>>>(src + 2 * n2, dst + 2 * n2, 1);
+    } else {
+        k_copy8<<<blocks, 512, 0, st>>>(src, dst, count);
+    }
     trace_count(1);
     return cudaGetLastError();
 }

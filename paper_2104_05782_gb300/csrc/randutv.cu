@@ -1293,6 +1293,17 @@ struct ModeArgs {
     int64_t tr_stride = 1;
 };
 
+// The device address of page-locked host memory (registered or allocated by
+// CUDA), or null for any other pointer.
+const void* pinned_device_address(const void* host) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost) ? a.devicePointer : nullptr;
+}
+
 randutv_status factor_impl(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q, uint64_t seed, double* U,
                            double* T, double* V, int prec, void* stream, void* workspace, size_t ws_bytes,
                            int64_t stop_after, int* info, const ModeArgs& ma, const FactorOpts& fo = FactorOpts{}) {
@@ -1579,19 +1590,33 @@ randutv_status randutv_factor_host(int64_t m, int64_t n, const double* A, int64_
     if (U && cached_buffer(dev, 1, std::max<size_t>(bytesU, 8), &dU) != cudaSuccess) return RANDUTV_ENOMEM;
     if (V && cached_buffer(dev, 2, std::max<size_t>(bytesV, 8), &dV) != cudaSuccess) return RANDUTV_ENOMEM;
     cudaStream_t st = nullptr;  // legacy default stream
-    if (bytesT > 0) {  // one contiguous copy when A has no padding, else a pitched copy
-        const cudaError_t e = (lda == m)
-                                  ? cudaMemcpyAsync(dA, A, bytesT, cudaMemcpyHostToDevice, st)
-                                  : cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda,
-                                                      sizeof(double) * m, n, cudaMemcpyHostToDevice, st);
+    const int sms = device_sms(dev);
+    if (bytesT > 0) {
+        // pinned host memory: the SMs copy from it directly; otherwise one
+        // contiguous DMA copy when A has no padding, else a pitched one
+        const double* hA = (const double*)pinned_device_address(A);
+        cudaError_t e;
+        if (hA && lda == m)
+            e = copy_flat(hA, (double*)dA, m * n, sms, st);
+        else if (hA)
+            e = copy_matrix(hA, lda, (double*)dA, m, m, n, st);
+        else
+            e = (lda == m) ? cudaMemcpyAsync(dA, A, bytesT, cudaMemcpyHostToDevice, st)
+                           : cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m,
+                                               n, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return RANDUTV_ECUDA;
     }
     randutv_status rs = randutv_factor_ex(m, n, (double*)dA, m, b, q, seed, (double*)dU, (double*)dA, (double*)dV,
                                           prec, st, nullptr, 0, -1, nullptr);
     if ((rs == RANDUTV_OK || rs == RANDUTV_ENOCONV) && bytesT > 0) {
-        if (cudaMemcpyAsync(T, dA, bytesT, cudaMemcpyDeviceToHost, st) != cudaSuccess) return RANDUTV_ECUDA;
-        if (U && cudaMemcpyAsync(U, dU, bytesU, cudaMemcpyDeviceToHost, st) != cudaSuccess) return RANDUTV_ECUDA;
-        if (V && cudaMemcpyAsync(V, dV, bytesV, cudaMemcpyDeviceToHost, st) != cudaSuccess) return RANDUTV_ECUDA;
+        auto out = [&](double* host, const void* src, size_t bytes) -> cudaError_t {
+            double* h = (double*)pinned_device_address(host);
+            return h ? copy_flat((const double*)src, h, (int64_t)(bytes / sizeof(double)), sms, st)
+                     : cudaMemcpyAsync(host, src, bytes, cudaMemcpyDeviceToHost, st);
+        };
+        if (out(T, dA, bytesT) != cudaSuccess) return RANDUTV_ECUDA;
+        if (U && out(U, dU, bytesU) != cudaSuccess) return RANDUTV_ECUDA;
+        if (V && out(V, dV, bytesV) != cudaSuccess) return RANDUTV_ECUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return RANDUTV_ECUDA;
     }
     return rs;

@@ -192,3 +192,21 @@ def test_host_entry_point_padded_lda(rutv):
         outs.append((U, T, V))
     for x, y in zip(*outs):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("pad", [0, 5])
+def test_host_entry_point_pinned_buffers(rutv, pad):
+    """Page-locked host buffers go through the library's copy kernels (their
+    device addresses) instead of DMA copies: the same bits as the
+    device-resident call, with and without a padded leading dimension."""
+    m, n, b, q = 300, 220, 32, 1
+    A = synthetic.test_matrix(m, n, "geometric10", 28, 29)
+    big = torch.full((n, m + pad), float("nan"), dtype=torch.float64).pin_memory()
+    big[:, :m] = torch.from_numpy(np.ascontiguousarray(A.T))
+    Th = torch.empty((n, m), dtype=torch.float64).pin_memory()
+    Uh = torch.empty((m, m), dtype=torch.float64).pin_memory()
+    Vh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    assert rutv.randutv_factor_host(m, n, big, m + pad, b, q, 2, Uh, Th, Vh) == rutv.RANDUTV_OK
+    got = gpu_factor(rutv, A, b, q, 2)
+    assert np.array_equal(Th.numpy().T, got[1])
+    assert np.array_equal(Uh.numpy().T, got[0]) and np.array_equal(Vh.numpy().T, got[2])
