@@ -53,6 +53,9 @@ def measured_peak(key: str, fallback: float) -> float:
 
 # ncu: 222.2 MB of DRAM traffic for the 4.295 GFLOP rank-128 update launch (4096^2)
 GEMM_F64_DRAM_BYTES_PER_FLOP = 222.2e6 / (2.0 * 4096 * 4096 * 128)
+# ncu: 531 MB of DRAM traffic for the three emulated products of the 4096^2
+# right update (8.72 GFLOP of FP64-equivalent work)
+OZ_DRAM_BYTES_PER_FP64_FLOP = 531.0e6 / 8.72e9
 
 
 def randutv_flops(m: int, n: int, b: int, q: int, uv: bool = True) -> float:
@@ -533,7 +536,10 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
             "kernel": "k_oz_gemm (FP64 product emulated by %d BF16 digit products on tcgen05, "
                       "with its digit split)" % OZ_PAIRS,
             "bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
-            "frac": (achieved / bf16_peak) if achieved else None, "traffic": None,
+            "frac": (achieved / bf16_peak) if achieved else None,
+            "traffic": OZ_DRAM_BYTES_PER_FP64_FLOP * g_fl / max(g_launch, 1),
+            "traffic_source": "ncu dram__bytes_read+write of k_oz_gemm on the 4096^2 right update (0.061 B per "
+                              "FP64-equivalent flop), scaled by the average work per launch",
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
             "fp64_equivalent_tflops": g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else None,
             "launches": g_launch, "share_of_traced_time": g_ms / tot_ms if tot_ms else None,
