@@ -258,8 +258,8 @@ randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64
  * sketch of every block step, a small network (16 -> 64 -> 64 -> 4, GELU,
  * FP32, softmax over q in {0,1,2,3}) picks q from 16 features: the decay of
  * the previous block's panel-QR R diagonal and of the Householder R diagonal of the
- * q = 0 sketch (compressed to 2b rows by a second Gaussian sketch, a
- * subspace embedding), each as log10(|d_j| / |d_0|) at j = 0, w/8, ..., 7w/8.
+ * q = 0 sketch (compressed to 2b rows by a CountSketch with random signs),
+ * each as log10(|d_j| / |d_0|) at j = 0, w/8, ..., 7w/8.
  * The q = 0 product is reused by the chosen iterations.
  *   model   : HOST array of randutv_learnq_model_floats() floats (layout:
  *             W1[16][64] b1[64] W2[64][64] b2[64] W3[64][4] b3[4] mu[16] sd[16],
@@ -267,7 +267,7 @@ randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64
  *             A non-finite network output also falls back to q = 2.  The
  *             network predicts a distribution over the smallest adequate q;
  *             the step runs the smallest q whose cumulative predicted
- *             probability reaches 0.95.
+ *             probability reaches 0.99.
  *   q_used  : HOST array of ceil(n / b) ints (or NULL): the q chosen per
  *             sketch step, -1 for the final block (no sketch).
  * Other arguments as randutv_factor / randutv_factor_ex.  The choice stays

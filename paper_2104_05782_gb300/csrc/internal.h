@@ -118,6 +118,10 @@ int learnq_nparam();
 // compressed q = 0 sketch.
 cudaError_t learnq_features(const double* dprev, int64_t dstride, int wprev, const double* R, int64_t ldr, int w,
                             float* f, cudaStream_t st);
+// E (e x w, ld e) := S Y with S the CountSketch r -> r mod e, sign from a
+// hash of key + r (Y: L x w, ld ldy).
+cudaError_t countsketch(const double* Y, int64_t ldy, int64_t L, int w, int e, uint64_t key, double* E,
+                        cudaStream_t st);
 // rdiag (w doubles) := |R_jj| of the Householder QR of E (e x w, ld lde) in
 // FP32 in one block; e <= 256, w <= 128.
 cudaError_t feature_rdiag(const double* E, int64_t lde, int e, int w, double* rdiag, cudaStream_t st);

@@ -13,9 +13,9 @@
 //              (block 0: copies of f[8..15]);
 //   f[8..15] = log10(|R_jj| / |R_00|) at the same j, with R the Householder
 //              R of the q = 0 sketch Y0 = T22^T G compressed to at most 2b
-//              rows by a second Gaussian sketch (Omega Y0, Omega 2b x n'; a
-//              subspace embedding, so the decay of R is kept to a constant
-//              factor; Y0 itself when n' <= 2b), factored in FP32 (b <= 128).
+//              rows by a structured CountSketch (row r to row r mod 2b with
+//              a random sign; Y0 itself when n' <= 2b), factored in FP32
+//              (b <= 128).
 // Training kernels: per-sample forward, per-sample backward, gradient
 // reductions over the batch in a fixed order (deterministic, no atomics),
 // and Adam.  Cross-entropy loss averaged over the batch.
@@ -32,7 +32,7 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NI * NH, OFF_W2 = OFF_B1 + NH, OFF_B
               OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NH * NO, OFF_MU = OFF_B3 + NO, OFF_SD = OFF_MU + NI,
               NPARAM = OFF_SD + NI;
 constexpr int NTRAIN = OFF_MU;  // trainable parameters (mu, sd are fixed)
-constexpr float kLearnqConfidence = 0.95f;
+constexpr float kLearnqConfidence = 0.99f;
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_d(float x) {
@@ -158,21 +158,71 @@ __global__ void __launch_bounds__(FQR_THREADS) k_feature_rdiag32(const double* _
     }
 }
 
+// E (e x w, ld e) = S Y (Y: L x w, ld ldy): the structured CountSketch
+// that sends row r of Y to row r mod e of E with the sign of bit 0 of
+// splitmix64(key + r) (Steele, Lea, Flood 2014).  One thread per entry of
+// E sums its rows in order: deterministic, no atomics.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+__global__ void k_countsketch(const double* __restrict__ Y, int64_t ldy, int64_t L, int w, int e, uint64_t key,
+                              double* __restrict__ E) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)e * w) return;
+    const int k = (int)(t % e), c = (int)(t / e);
+    double s = 0.0;
+    for (int64_t r = k; r < L; r += e) {
+        const double y = Y[r + c * ldy];
+        s += (splitmix64(key + (uint64_t)r) & 1ull) ? -y : y;
+    }
+    E[k + (int64_t)c * e] = s;
+}
+
 // The network predicts a distribution over the smallest adequate q.  The
 // choice is risk-controlled: the smallest q whose cumulative predicted
 // probability P(q_min <= q) reaches `confidence` (a plain argmax would accept
 // every block the network is unsure about).  No model or a non-finite output
 // gives `fallback`.
-__global__ void k_learnq_infer(const float* __restrict__ P, const float* __restrict__ f, int fallback,
-                               float confidence, int* q, int* qlog) {
-    if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(NH) k_learnq_infer(const float* __restrict__ P, const float* __restrict__ f,
+                                                     int fallback, float confidence, int* q, int* qlog) {
+    // one thread per hidden unit; each sum runs over the inputs in the same
+    // order as mlp_forward
+    __shared__ float x[NI], h1[NH], h2[NH], lg[NO];
+    const int t = threadIdx.x;
     if (P == nullptr) {
-        *q = fallback;
-        if (qlog) *qlog = fallback;
+        if (t == 0) {
+            *q = fallback;
+            if (qlog) *qlog = fallback;
+        }
         return;
     }
-    float pre1[NH], h1[NH], pre2[NH], h2[NH], lg[NO];
-    mlp_forward(P, f, pre1, h1, pre2, h2, lg);
+    if (t < NI) {
+        const float sd = P[OFF_SD + t];
+        x[t] = (f[t] - P[OFF_MU + t]) / (sd > 0.f ? sd : 1.f);
+    }
+    __syncthreads();
+    {
+        float a = P[OFF_B1 + t];
+        for (int i = 0; i < NI; ++i) a = fmaf(x[i], P[OFF_W1 + i * NH + t], a);
+        h1[t] = gelu(a);
+    }
+    __syncthreads();
+    {
+        float a = P[OFF_B2 + t];
+        for (int i = 0; i < NH; ++i) a = fmaf(h1[i], P[OFF_W2 + i * NH + t], a);
+        h2[t] = gelu(a);
+    }
+    __syncthreads();
+    if (t < NO) {
+        float a = P[OFF_B3 + t];
+        for (int i = 0; i < NH; ++i) a = fmaf(h2[i], P[OFF_W3 + i * NO + t], a);
+        lg[t] = a;
+    }
+    __syncthreads();
+    if (t != 0) return;
     bool finite = true;
     for (int k = 0; k < NO; ++k) finite &= isfinite(lg[k]);
     if (!finite) {
@@ -298,6 +348,15 @@ __global__ void k_sum_loss(const float* __restrict__ l, int N, float* out) {
 
 int learnq_nparam() { return NPARAM; }
 
+cudaError_t countsketch(const double* Y, int64_t ldy, int64_t L, int w, int e, uint64_t key, double* E,
+                        cudaStream_t st) {
+    const int64_t total = (int64_t)e * w;
+    if (total <= 0) return cudaSuccess;
+    k_countsketch<<<(unsigned)cdiv(total, 128), 128, 0, st>>>(Y, ldy, L, w, e, key, E);
+    trace_count(1);
+    return cudaGetLastError();
+}
+
 cudaError_t feature_rdiag(const double* E, int64_t lde, int e, int w, double* rdiag, cudaStream_t st) {
     if (e > 256 || w > 128 || e < 1 || w < 1) return cudaErrorInvalidValue;
     const size_t shm = sizeof(float) * (size_t)(e + 1) * w;
@@ -321,7 +380,7 @@ cudaError_t learnq_features(const double* dprev, int64_t dstride, int wprev, con
 }
 
 cudaError_t learnq_infer(const float* P, const float* f, int fallback, int* q, int* qlog, cudaStream_t st) {
-    k_learnq_infer<<<1, 32, 0, st>>>(P, f, fallback, kLearnqConfidence, q, qlog);
+    k_learnq_infer<<<1, NH, 0, st>>>(P, f, fallback, kLearnqConfidence, q, qlog);
     trace_count(1);
     return cudaGetLastError();
 }

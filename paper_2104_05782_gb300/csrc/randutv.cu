@@ -948,27 +948,22 @@ cudaError_t fp64_iterate(Ctx& c, int64_t k0, double* Y, int iters) {
     return cudaSuccess;
 }
 
-// Step index of the Gaussian draws that compress the sketch for the
-// features, far from the sketch steps' own indices.
+// Added to the step index in the key of the CountSketch signs of the features.
 constexpr int64_t kFeatureDrawStep = (int64_t)1 << 40;
 
 // Features of block step i (needs Y0 = T22^T G in c.w.Y): the Householder R
-// of E = Omega Y0 (2b x b, two Gaussian draws Omega_1, Omega_2 of b rows each;
-// E = Y0 when n' <= 2b), in FP32 in one block for b <= 128, and the previous
-// block's R diagonal (from its panel QR), read from dprev[j * dstride].
+// of E = S Y0 (2b x b, S the structured CountSketch r -> r mod 2b with random
+// signs; E = Y0 when n' <= 2b), in FP32 in one block for b <= 128, and the
+// previous block's R diagonal (from its panel QR), read from dprev[j * dstride].
 cudaError_t block_features(Ctx& c, int64_t i, int64_t np, const double* dprev, int64_t dstride) {
     const int b = c.b;
-    TraceScope ts("learnq_features", 4.0 * (double)np * b * b, 16.0 * (double)np * b, c.st);
+    TraceScope ts("learnq_features", 0.0, 8.0 * (double)np * b, c.st);
     const int64_t e = std::min<int64_t>(2 * (int64_t)b, np);
     double* E = c.w.X2;  // e x b, ld e
-    if (np <= 2 * (int64_t)b) {
+    if (np <= 2 * (int64_t)b)
         CK(copy_matrix(c.w.Y, np, E, e, np, b, c.st));
-    } else {
-        for (int h = 0; h < 2; ++h) {
-            CK(gaussian_f64(c.seed, kFeatureDrawStep + 2 * i + h, np, b, c.w.Z, np, c.st));
-            CK(gemm(c, "learnq_features", true, false, b, b, np, 1.0, c.w.Z, np, c.w.Y, np, 0.0, E + h * b, e));
-        }
-    }
+    else
+        CK(countsketch(c.w.Y, np, np, b, (int)e, c.seed ^ (uint64_t)(kFeatureDrawStep + i), E, c.st));
     if (e <= 256 && b <= 128) {  // |R_jj| of E by a one-block FP32 QR
         CK(feature_rdiag(E, e, e, b, c.w.sdiag, c.st));
         return learnq_features(dprev, dstride, dprev ? b : 0, c.w.sdiag, 0, b, c.w.feat, c.st);
