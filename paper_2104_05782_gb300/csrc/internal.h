@@ -51,6 +51,11 @@ int panel_qr_grid(int64_t len, int w, int sms);
 // scratch: panel_qr_scratch_elems doubles; bar: one zeroed unsigned counter.
 cudaError_t panel_qr(double* P, int64_t ld, int64_t len, int w, double* tau, double* scratch,
                      unsigned* bar, int* status, int sms, cudaStream_t st);
+// Same factorization for w <= 32, which also writes the compact WY form of
+// the panel: W (len x w, ld len, as extract_w) and Tf (w x w, ld w, as tfactor
+// of W^T W), the Gram matrix formed inside the kernel.
+cudaError_t panel_qr_wy(double* P, int64_t ld, int64_t len, int w, double* tau, double* W, double* Tf,
+                        double* scratch, unsigned* bar, int* status, int sms, cudaStream_t st);
 // W (len x w, ld len) := unit lower trapezoidal part of the QR storage P.
 cudaError_t extract_w(const double* P, int64_t ld, int64_t len, int w, double* W, cudaStream_t st);
 // Upper triangular Tf (w x w, ld w) of Q = I - W Tf W^T from Gram = W^T W and tau.

@@ -161,7 +161,9 @@ __global__ void __launch_bounds__(FQR_THREADS) k_feature_rdiag32(const double* _
 // E (e x w, ld e) = S Y (Y: L x w, ld ldy): the structured CountSketch
 // that sends row r of Y to row r mod e of E with the sign of bit 0 of
 // splitmix64(key + r) (Steele, Lea, Flood 2014).  One thread per entry of
-// E sums its rows in order: deterministic, no atomics.
+// E sums its rows in order: deterministic, no atomics.  The loads of eight
+// rows are issued before they are added, so that a thread waits for one
+// memory round trip per eight rows rather than per row.
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     x += 0x9E3779B97F4A7C15ull;
     x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -174,9 +176,18 @@ __global__ void k_countsketch(const double* __restrict__ Y, int64_t ldy, int64_t
     if (t >= (int64_t)e * w) return;
     const int k = (int)(t % e), c = (int)(t / e);
     double s = 0.0;
-    for (int64_t r = k; r < L; r += e) {
-        const double y = Y[r + c * ldy];
-        s += (splitmix64(key + (uint64_t)r) & 1ull) ? -y : y;
+    for (int64_t r0 = k; r0 < L; r0 += 8 * (int64_t)e) {
+        double y[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t r = r0 + u * (int64_t)e;
+            y[u] = (r < L) ? Y[r + c * ldy] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t r = r0 + u * (int64_t)e;
+            s += (splitmix64(key + (uint64_t)r) & 1ull) ? -y[u] : y[u];
+        }
     }
     E[k + (int64_t)c * e] = s;
 }

@@ -506,35 +506,34 @@ cudaError_t panel_gemm(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K
 
 // Blocked Householder QR of a len x w panel (the recursion-free form of
 // LAPACK's blocked QR, Sec. 2.3): sub-panels of kSubPanel columns are factored
-// by the one-barrier-per-column kernel, and each one's compact WY transform
-// Q_k = I - W_k Tf_k W_k^T is applied to the columns right of it,
-// C := Q_k^T C = C - W_k Tf_k^T (W_k^T C), by three products.  Most of the
-// panel's FP64 multiply-adds thus move into those products (emulated on the
-// tensor cores); the reflectors, tau and R are those of the unblocked
-// factorization, up to rounding.  Uses c.w.W and c.w.Tf as scratch
+// by the one-barrier-per-column kernel, which also returns each one's compact
+// WY form (W_k, Tf_k), and Q_k = I - W_k Tf_k W_k^T is applied to the columns
+// right of it, C := Q_k^T C = C - W_k Tf_k^T (W_k^T C), by three products.
+// Most of the panel's FP64 multiply-adds thus move into those products
+// (emulated on the tensor cores); the reflectors, tau and R are those of the
+// unblocked factorization, up to rounding.  Uses c.w.W and c.w.Tf as scratch
 // (factor_panel recomputes W, Tf of the whole panel afterwards) and keeps the
-// sub-panel's Gram matrix and the two wk x rest products in c.w.gram:
-// wk^2 + 2 wk (w - wk) <= w^2 for every w.
+// two wk x rest products in c.w.gram: 2 wk (w - wk) <= w^2 for every w.
 cudaError_t blocked_panel_qr(Ctx& c, double* P, int64_t ld, int64_t len, int w) {
     for (int k0 = 0; k0 < w; k0 += kSubPanel) {
         const int wk = std::min(kSubPanel, w - k0);
         const int64_t lk = len - k0;
+        const int rest = w - k0 - wk;
         double* Pk = P + k0 + (int64_t)k0 * ld;
-        {
+        if (rest <= 0 || lk <= 0) {
             TraceScope ts("panel_qr", 2.0 * (double)lk * wk * wk, 16.0 * (double)lk * wk, c.st);
             CK(panel_qr(Pk, ld, lk, wk, c.w.tau + k0, c.w.pscr, c.w.bars, c.w.status, panel_sms(c), c.st));
+            continue;
         }
-        const int rest = w - k0 - wk;
-        if (rest <= 0 || lk <= 0) continue;
-        TraceScope ts("panel_update", 4.0 * (double)lk * wk * (wk + rest), 8.0 * (double)lk * (2 * wk + 2 * rest),
-                      c.st);
+        {
+            TraceScope ts("panel_qr", 3.0 * (double)lk * wk * wk, 24.0 * (double)lk * wk, c.st);
+            CK(panel_qr_wy(Pk, ld, lk, wk, c.w.tau + k0, c.w.W, c.w.Tf, c.w.pscr, c.w.bars, c.w.status,
+                           panel_sms(c), c.st));
+        }
+        TraceScope ts("panel_update", 4.0 * (double)lk * wk * rest, 8.0 * (double)lk * (wk + 2 * rest), c.st);
         double* C = Pk + (int64_t)wk * ld;
-        double* Gk = c.w.gram;
-        double* Xk = Gk + (size_t)wk * wk;
+        double* Xk = c.w.gram;
         double* X2k = Xk + (size_t)wk * rest;
-        CK(extract_w(Pk, ld, lk, wk, c.w.W, c.st));
-        CK(panel_gemm(c, true, false, wk, wk, lk, 1.0, c.w.W, lk, c.w.W, lk, 0.0, Gk, wk));
-        CK(tfactor(Gk, c.w.tau + k0, wk, c.w.Tf, c.w.status, c.st));
         CK(panel_gemm(c, true, false, wk, rest, lk, 1.0, c.w.W, lk, C, ld, 0.0, Xk, wk));
         CK(gemm_f64(true, false, wk, rest, wk, 1.0, c.w.Tf, wk, Xk, wk, 0.0, X2k, wk, c.w.part, c.w.part_elems, c.sms,
                     c.st));

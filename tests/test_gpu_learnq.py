@@ -167,7 +167,12 @@ def test_trained_network_gain_over_q2(rutv):
     the training mix, factored with FP64 (DMMA) products: the trained network
     must use strictly fewer power iterations and less time than fixed q = 2
     over the set, and every T_ii / sigma_i above the noise floor must stay
-    within 5% of the q = 2 result or closer to 1."""
+    within 5% of the q = 2 result or closer to 1.  One stretch of the gap
+    spectrum is left out of the comparison: the indices past the gap inside
+    the block that straddles it.  There the q = 2 sketch weighs the directions
+    past the gap at (1e-3)^5 = 1e-15 of the cluster's, below FP64 rounding, so
+    T_ii is set by rounding in every run (fixed q included) and any change of
+    the operation order, such as another q in an earlier block, moves it."""
     model = rutv.load_qnet()
     if model is None:
         pytest.skip("no trained network shipped (run python -m paper_2104_05782_gb300.learnq_train)")
@@ -203,12 +208,16 @@ def test_trained_network_gain_over_q2(rutv):
         nrm = np.linalg.norm(A)
         assert np.linalg.norm(A - host(U) @ Th @ host(V).T) / nrm <= utv_bound(n)
         keep = s > 1e3 * 2.0 ** -53 * s[0]
+        if kind == "gap":
+            k_gap = n // 10
+            keep[k_gap:(k_gap // b + 1) * b] = False
         r_l = np.diag(Th)[keep] / s[keep]
         r_2 = np.diag(T2h)[keep] / s[keep]
         dev_ = np.abs(r_l / r_2 - 1)
         ok = (dev_ <= 0.05) | (np.abs(np.log(r_l)) <= np.abs(np.log(r_2)))
         print("learned-q %s: q used %s; %d vs %d iterations, %.4f s vs %.4f s; max dev %.3g; "
-              "%d of %d indices fail" % (kind, qu, il, i2, dt_l, dt_2, dev_.max(), int((~ok).sum()), ok.size))
+              "%d of %d indices fail %s" % (kind, [int(x) for x in qu], il, i2, dt_l, dt_2, dev_.max(),
+                                           int((~ok).sum()), ok.size, np.flatnonzero(keep)[~ok][:20].tolist()))
         assert ok.all(), kind
     print("learned-q total: %d vs %d power iterations, %.3f s vs %.3f s" % (iters_l, iters_2, t_l, t_2))
     assert iters_l < iters_2
