@@ -259,7 +259,9 @@ randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64
  * FP32, softmax over q in {0,1,2,3}) picks q from 16 features: the decay of
  * the previous block's panel-QR R diagonal and of the Householder R diagonal of the
  * q = 0 sketch (compressed to 2b rows by a CountSketch with random signs),
- * each as log10(|d_j| / |d_0|) at j = 0, w/8, ..., 7w/8.
+ * each as log10(|d_j| / |d_0|) at j = w/8, ..., 7w/8, and the level of the
+ * trailing matrix, log10 of the compressed sketch's Frobenius norm over the
+ * first block's (it tells a block of rounding noise from a cluster).
  * The q = 0 product is reused by the chosen iterations.
  *   model   : HOST array of randutv_learnq_model_floats() floats (layout:
  *             W1[16][64] b1[64] W2[64][64] b2[64] W3[64][4] b3[4] mu[16] sd[16],

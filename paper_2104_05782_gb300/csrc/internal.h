@@ -119,17 +119,19 @@ cudaError_t cholqr32(float* X, int64_t L, int b, int passes, uint16_t* Xb, int64
 // ---- learned q (learnq.cu) --------------------------------------------------
 int learnq_nparam();
 // Features of a block step from the previous block's diagonal (dprev[j * dstride],
-// j < wprev; wprev = 0 for the first block) and the QR storage R of the
-// compressed q = 0 sketch.
+// j < wprev; wprev = 0 for the first block of the call) and the QR storage R of
+// the compressed q = 0 sketch.  lvl[0]: the sketch's Frobenius norm when
+// have_level (else formed from R), lvl[1]: the first block's, kept here.
 cudaError_t learnq_features(const double* dprev, int64_t dstride, int wprev, const double* R, int64_t ldr, int w,
-                            float* f, cudaStream_t st);
+                            float* f, double* lvl, bool have_level, cudaStream_t st);
 // E (e x w, ld e) := S Y with S the CountSketch r -> r mod e, sign from a
 // hash of key + r (Y: L x w, ld ldy).
 cudaError_t countsketch(const double* Y, int64_t ldy, int64_t L, int w, int e, uint64_t key, double* E,
                         cudaStream_t st);
 // rdiag (w doubles) := |R_jj| of the Householder QR of E (e x w, ld lde) in
-// FP32 in one block; e <= 256, w <= 128.
-cudaError_t feature_rdiag(const double* E, int64_t lde, int e, int w, double* rdiag, cudaStream_t st);
+// FP32 in one block; *level := ||E||_F (FP64); e <= 256, w <= 128.
+cudaError_t feature_rdiag(const double* E, int64_t lde, int e, int w, double* rdiag, double* level,
+                          cudaStream_t st);
 // q (device) := the network's choice; also written to *qlog when qlog != null.
 cudaError_t learnq_infer(const float* P, const float* f, int fallback, int* q, int* qlog, cudaStream_t st);
 size_t learnq_train_scratch_floats(int N);

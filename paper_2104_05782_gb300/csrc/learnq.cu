@@ -11,11 +11,17 @@
 //              singular values, and is ready before the block's b x b SVD, so
 //              that SVD can overlap the next step) at j = 0, w/8, ..., 7w/8
 //              (block 0: copies of f[8..15]);
-//   f[8..15] = log10(|R_jj| / |R_00|) at the same j, with R the Householder
-//              R of the q = 0 sketch Y0 = T22^T G compressed to at most 2b
-//              rows by a structured CountSketch (row r to row r mod 2b with
-//              a random sign; Y0 itself when n' <= 2b), factored in FP32
-//              (b <= 128).
+//   f[9..15] = log10(|R_jj| / |R_00|) at j = w/8, ..., 7w/8, with R the
+//              Householder R of the q = 0 sketch Y0 = T22^T G compressed to
+//              at most 2b rows by a structured CountSketch (row r to row
+//              r mod 2b with a random sign; Y0 itself when n' <= 2b),
+//              factored in FP32 (b <= 128);
+//   f[8]     = log10(||E||_F / ||E_0||_F), E that compressed sketch and E_0
+//              the first block's: the level of the trailing matrix against
+//              the whole (E[||S T22^T g||^2] = ||T22||_F^2 for a Gaussian g),
+//              which tells a block of rounding noise (every choice of q is
+//              as good) from a block inside a cluster of equal singular
+//              values (flat ratios in both cases).
 // Training kernels: per-sample forward, per-sample backward, gradient
 // reductions over the batch in a fixed order (deterministic, no atomics),
 // and Adam.  Cross-entropy loss averaged over the batch.
@@ -68,17 +74,41 @@ __device__ void mlp_forward(const float* P, const float* xin, float* pre1, float
 
 // Features of a block step (see the file comment).  R_jj are read from the
 // QR storage of the compressed sketch (ld ldr); the previous block's d_j from
-// dprev[j * dstride] (wprev = 0: first block).
+// dprev[j * dstride] (wprev = 0: first block of the call).  lvl[0] is the
+// Frobenius norm of the compressed sketch when its caller computed it
+// (have_level), else it is formed here from the upper triangle of the QR
+// storage (the R factor has the same norm); lvl[1] keeps the first block's.
 __global__ void k_learnq_features(const double* __restrict__ dprev, int64_t dstride, int wprev,
-                                  const double* __restrict__ R, int64_t ldr, int w, float* __restrict__ f) {
+                                  const double* __restrict__ R, int64_t ldr, int w, float* __restrict__ f,
+                                  double* __restrict__ lvl, int have_level) {
     const int t = threadIdx.x;
-    if (t < 8) {
+    __shared__ double s_level;
+    if (t == 0) s_level = have_level ? lvl[0] : 0.0;
+    if (!have_level) {  // one warp: column j of the upper triangle, fixed order
+        double acc = 0.0;
+        for (int j = t; j < w; j += 32)
+            for (int i = 0; i <= j; ++i) {
+                const double x = R[i + (int64_t)j * ldr];
+                acc = fma(x, x, acc);
+            }
+        acc = warp_sum(acc);
+        if (t == 0) s_level = sqrt(acc);
+    }
+    __syncwarp();
+    if (t > 0 && t < 8) {
         int j = (t * w) / 8;
         double r0 = fabs(R[0]), rj = fabs(R[j + (int64_t)j * ldr]);
         float v = (r0 > 0.0 && rj > 0.0) ? (float)log10(rj / r0) : -16.0f;
         f[8 + t] = fmaxf(v, -16.0f);
     }
-    __syncthreads();
+    if (t == 0) {
+        const double level = s_level;
+        if (wprev <= 0) lvl[1] = level;
+        const double ref = (wprev <= 0) ? level : lvl[1];
+        const float v = (level > 0.0 && ref > 0.0) ? (float)log10(level / ref) : -16.0f;
+        f[8] = fmaxf(v, -16.0f);
+    }
+    __syncwarp();
     if (t < 8) {
         if (wprev <= 0) {
             f[t] = f[8 + t];
@@ -100,21 +130,33 @@ __global__ void k_learnq_features(const double* __restrict__ dprev, int64_t dstr
 // rounding; the features clip there consistently in training and use.
 constexpr int FQR_THREADS = 1024;
 __global__ void __launch_bounds__(FQR_THREADS) k_feature_rdiag32(const double* __restrict__ E, int64_t lde, int e, int w,
-                                                                 double* __restrict__ rdiag) {
+                                                                 double* __restrict__ rdiag, double* __restrict__ level) {
     extern __shared__ float fa[];  // e x w, column stride ld = e + 1
-    __shared__ float s_tau, s_inv;
-    __shared__ double s_max[32];
+    __shared__ float s_tau;
+    __shared__ double s_max[32], s_ss[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ld = e + 1;
-    double mx = 0.0;
-    for (int t = tid; t < e * w; t += FQR_THREADS) mx = fmax(mx, fabs(E[(t % e) + (int64_t)(t / e) * lde]));
+    double mx = 0.0, ss = 0.0;  // largest |E| and the sum of squares (the level), fixed order
+    for (int t = tid; t < e * w; t += FQR_THREADS) {
+        const double x = E[(t % e) + (int64_t)(t / e) * lde];
+        mx = fmax(mx, fabs(x));
+        ss = fma(x, x, ss);
+    }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) s_max[warp] = mx;
+    ss = warp_sum(ss);
+    if (lane == 0) {
+        s_max[warp] = mx;
+        s_ss[warp] = ss;
+    }
     __syncthreads();
     if (tid == 0) {
-        double m = 0.0;
-        for (int k = 0; k < FQR_THREADS / 32; ++k) m = fmax(m, s_max[k]);
+        double m = 0.0, q = 0.0;
+        for (int k = 0; k < FQR_THREADS / 32; ++k) {
+            m = fmax(m, s_max[k]);
+            q += s_ss[k];
+        }
         s_max[0] = m;
+        level[0] = sqrt(q);
     }
     __syncthreads();
     const double scale = s_max[0] > 0.0 ? 1.0 / s_max[0] : 1.0;
@@ -140,7 +182,6 @@ __global__ void __launch_bounds__(FQR_THREADS) k_feature_rdiag32(const double* _
             if (lane == 0) {
                 rdiag[j] = fabs((double)beta);
                 s_tau = tau;
-                s_inv = inv;
             }
         }
         __syncthreads();
@@ -368,7 +409,8 @@ cudaError_t countsketch(const double* Y, int64_t ldy, int64_t L, int w, int e, u
     return cudaGetLastError();
 }
 
-cudaError_t feature_rdiag(const double* E, int64_t lde, int e, int w, double* rdiag, cudaStream_t st) {
+cudaError_t feature_rdiag(const double* E, int64_t lde, int e, int w, double* rdiag, double* level,
+                          cudaStream_t st) {
     if (e > 256 || w > 128 || e < 1 || w < 1) return cudaErrorInvalidValue;
     const size_t shm = sizeof(float) * (size_t)(e + 1) * w;
     static bool configured = false;
@@ -378,14 +420,14 @@ cudaError_t feature_rdiag(const double* E, int64_t lde, int e, int w, double* rd
         if (err != cudaSuccess) return err;
         configured = true;
     }
-    k_feature_rdiag32<<<1, FQR_THREADS, shm, st>>>(E, lde, e, w, rdiag);
+    k_feature_rdiag32<<<1, FQR_THREADS, shm, st>>>(E, lde, e, w, rdiag, level);
     trace_count(1);
     return cudaGetLastError();
 }
 
 cudaError_t learnq_features(const double* dprev, int64_t dstride, int wprev, const double* R, int64_t ldr, int w,
-                            float* f, cudaStream_t st) {
-    k_learnq_features<<<1, 32, 0, st>>>(dprev, dstride, wprev, R, ldr, w, f);
+                            float* f, double* lvl, bool have_level, cudaStream_t st) {
+    k_learnq_features<<<1, 32, 0, st>>>(dprev, dstride, wprev, R, ldr, w, f, lvl, have_level ? 1 : 0);
     trace_count(1);
     return cudaGetLastError();
 }

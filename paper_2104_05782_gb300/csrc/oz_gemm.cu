@@ -216,8 +216,8 @@ __global__ void k_oz_split(const double* __restrict__ X, int64_t ld, int R, int 
 // tiles in L2, and a CTA that starts late (its SM busy with a concurrent
 // kernel) simply takes fewer jobs.  The producer warp takes each job and
 // passes its index to the MMA and drain warps through a 4-slot ring.
-//   warp 8    : TMA producer (ring of OZ_AST A digit tiles, ring of OZ_BST
-//               stacked B digit sets)
+//   warp 8    : TMA producer (ring of OZ_AST stages of OZ_DPS A digit tiles,
+//               ring of OZ_BST stacked B digit sets)
 //   warp 9    : MMA issuer
 //   warps 0-7 : drain TMEM into double-float registers, then the epilogue
 // The 8 B digit planes of a k-block are stacked in shared memory (plane t =
@@ -225,13 +225,21 @@ __global__ void k_oz_split(const double* __restrict__ X, int64_t ld, int R, int 
 // of A digit s are ONE MMA of N = 32 (8 - s) writing accumulator columns
 // 32s .. 255, whose column block d then holds the digit sum d = s + t.  Two
 // 256-column accumulator buffers alternate per 128-deep chunk: the drain of
-// one chunk overlaps the MMAs of the next.
+// one chunk overlaps the MMAs of the next.  An A stage holds four digit
+// tiles (two stages per k-block): each barrier round trip between the
+// producer and MMA threads costs a few hundred cycles, as long as the MMAs
+// of one digit tile, so fewer and larger stages keep the tensor pipe fed
+// (a ten-stage ring of one tile each ran the split-K products 28%
+// slower).
 constexpr int OZ_TN = 32;                               // output columns per job
-constexpr int OZ_AST = 10;                              // A ring stages
+constexpr int OZ_DPS = 4;                               // A digit tiles per stage
+constexpr int OZ_AST = 10 / OZ_DPS;                     // A ring stages
+static_assert(OZ_S % OZ_DPS == 0, "whole digit tiles per stage");
 constexpr int OZ_BST = 2;                               // B ring stages
 constexpr int OZ_EPI = 8;                               // drain / epilogue warps
 constexpr int OZ_THREADS = (OZ_EPI + 2) * 32;
-constexpr int OZ_A_BYTES = OZ_TM * OZ_TK * 2;           // 16 KB
+constexpr int OZ_A_TILE = OZ_TM * OZ_TK * 2;            // 16 KB: one digit tile
+constexpr int OZ_A_BYTES = OZ_DPS * OZ_A_TILE;          // one A stage
 constexpr int OZ_BPLANE = OZ_TN * OZ_TK * 2;            // 4 KB
 constexpr int OZ_B_BYTES = OZ_S * OZ_BPLANE;            // 32 KB
 constexpr int OZ_ACC = OZ_S * OZ_TN;                    // 256 TMEM columns per buffer
@@ -276,7 +284,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
     if (gate_closed(gate)) return;
     extern __shared__ __align__(1024) uint8_t oz_raw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)oz_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* Abuf = sm;                                   // OZ_AST x 16 KB
+    uint8_t* Abuf = sm;                                   // OZ_AST x OZ_A_BYTES
     uint8_t* Bbuf = sm + OZ_AST * OZ_A_BYTES;             // OZ_BST x 32 KB
     __shared__ __align__(8) uint64_t bars[2 * OZ_AST + 2 * OZ_BST + 2 + 2 + 4 + 4];
     __shared__ uint32_t tslot[1];
@@ -346,11 +354,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                     for (int t = 0; t < OZ_S; ++t)
                         tma2d(Bbuf + sb * OZ_B_BYTES + t * OZ_BPLANE, &mapB, &b_full[sb], k, t * b_plane + b_row0 + n0);
                     ++ib;
-                    for (int s = 0; s < OZ_S; ++s) {
+                    for (int s0 = 0; s0 < OZ_S; s0 += OZ_DPS) {
                         const int sa = (int)(ia % OZ_AST);
                         if (!bar_wait(&a_empty[sa], (uint32_t)(((ia / OZ_AST) & 1) ^ 1))) { s_abort = 1; break; }
                         bar_expect(&a_full[sa], (uint32_t)OZ_A_BYTES);
-                        tma2d(Abuf + sa * OZ_A_BYTES, &mapA, &a_full[sa], k, s * a_plane + a_row0 + m0);
+                        for (int u = 0; u < OZ_DPS; ++u)
+                            tma2d(Abuf + sa * OZ_A_BYTES + u * OZ_A_TILE, &mapA, &a_full[sa], k,
+                                  (s0 + u) * a_plane + a_row0 + m0);
                         ++ia;
                     }
                 }
@@ -382,25 +392,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const __grid_constant
                     const int sb = (int)(ib % OZ_BST);
                     if (!bar_wait(&b_full[sb], (uint32_t)((ib / OZ_BST) & 1))) { s_abort = 1; break; }
                     const uint64_t db = desc_sw128(su32(Bbuf + sb * OZ_B_BYTES));
-                    for (int s = 0; s < OZ_S; ++s) {
+                    for (int s0 = 0; s0 < OZ_S; s0 += OZ_DPS) {
                         const int sa = (int)(ia % OZ_AST);
                         if (!bar_wait(&a_full[sa], (uint32_t)((ia / OZ_AST) & 1))) { s_abort = 1; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint64_t da = desc_sw128(su32(Abuf + sa * OZ_A_BYTES));
-                        const uint32_t dt = tmem + buf * OZ_ACC + (uint32_t)(s * OZ_TN);
-                        // M = 128, N = 32 (8 - s), BF16 x BF16 -> FP32, both K-major
-                        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                                               ((uint32_t)(((OZ_S - s) * OZ_TN) >> 3) << 17) |
-                                               ((uint32_t)(OZ_TM >> 4) << 24);
 #pragma unroll
-                        for (int k = 0; k < OZ_TK / 16; ++k) {
-                            const uint64_t ko = (uint64_t)((k * 32) >> 4);
-                            const uint32_t acc = (!first || s > 0 || k > 0) ? 1u : 0u;
-                            asm volatile(
-                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
-                                "l"(da + ko), "l"(db + ko), "r"(idesc), "r"(acc)
-                                : "memory");
+                        for (int u = 0; u < OZ_DPS; ++u) {
+                            const int s = s0 + u;
+                            const uint64_t da = desc_sw128(su32(Abuf + sa * OZ_A_BYTES + u * OZ_A_TILE));
+                            const uint32_t dt = tmem + buf * OZ_ACC + (uint32_t)(s * OZ_TN);
+                            // M = 128, N = 32 (8 - s), BF16 x BF16 -> FP32, both K-major
+                            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                                   ((uint32_t)(((OZ_S - s) * OZ_TN) >> 3) << 17) |
+                                                   ((uint32_t)(OZ_TM >> 4) << 24);
+#pragma unroll
+                            for (int k = 0; k < OZ_TK / 16; ++k) {
+                                const uint64_t ko = (uint64_t)((k * 32) >> 4);
+                                const uint32_t acc = (!first || s > 0 || k > 0) ? 1u : 0u;
+                                asm volatile(
+                                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dt),
+                                    "l"(da + ko), "l"(db + ko), "r"(idesc), "r"(acc)
+                                    : "memory");
+                            }
                         }
                         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                          su32(&a_empty[sa]))

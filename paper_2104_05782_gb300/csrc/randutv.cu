@@ -73,6 +73,7 @@ struct Workspace {
     double* dq;       // candidate diagonals, 4 x w (trace mode)
     double* rdiag;    // learned q / trace: the R diagonal of the last panel QR (w)
     double* sdiag;    // learned q / trace: |R_jj| of the compressed sketch (w)
+    double* level;    // learned q / trace: the compressed sketch's norm, and the first block's (2)
     float* qmodel;    // network parameters on the device
     void* oz;         // digit slices and exponents of the emulated FP64 products
     size_t oz_bytes;
@@ -178,7 +179,7 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec, bool qr_first
         lp ? sizeof(float) * (size_t)mx * npad : 0,                 // Y / Z in FP32
         lp ? sizeof(float) * cholqr_scratch_floats((int)npad, sms) : 0,
         lp ? sizeof(unsigned long long) : 0,                        // max |T22|
-        sizeof(float) * 32 + sizeof(double) * 6 * (size_t)wmax,     // learned-q features, q, candidates, R diagonals
+        sizeof(float) * 32 + sizeof(double) * (6 * (size_t)wmax + 2),  // learned-q features, q, candidates, R diagonals
         sizeof(float) * (size_t)learnq_nparam(),                    // learned-q model
         emulated_prec(prec) ? oz_work_bytes(mx, std::max<int64_t>(wmax, 128), mx) : 0,   // Ozaki digits
         emulated_prec(prec) ? oz_operand_bytes(m, n) : 0,                               // T(:, k0:n) by rows
@@ -236,6 +237,7 @@ Workspace carve(void* base, const Layout& L) {
     w.dq = (double*)(p + L.off[26] + sizeof(float) * 32);
     w.rdiag = w.dq + 4 * (size_t)L.wmax;
     w.sdiag = w.rdiag + (size_t)L.wmax;
+    w.level = w.sdiag + (size_t)L.wmax;
     w.qmodel = (float*)(p + L.off[27]);
     w.oz = (void*)(p + L.off[28]);
     w.oz_bytes = L.off[29] - L.off[28];
@@ -964,11 +966,11 @@ cudaError_t block_features(Ctx& c, int64_t i, int64_t np, const double* dprev, i
     else
         CK(countsketch(c.w.Y, np, np, b, (int)e, c.seed ^ (uint64_t)(kFeatureDrawStep + i), E, c.st));
     if (e <= 256 && b <= 128) {  // |R_jj| of E by a one-block FP32 QR
-        CK(feature_rdiag(E, e, e, b, c.w.sdiag, c.st));
-        return learnq_features(dprev, dstride, dprev ? b : 0, c.w.sdiag, 0, b, c.w.feat, c.st);
+        CK(feature_rdiag(E, e, e, b, c.w.sdiag, c.w.level, c.st));
+        return learnq_features(dprev, dstride, dprev ? b : 0, c.w.sdiag, 0, b, c.w.feat, c.w.level, true, c.st);
     }
     CK(panel_qr(E, e, e, b, c.w.tau, c.w.pscr, c.w.bars, c.w.status, panel_sms(c), c.st));
-    return learnq_features(dprev, dstride, dprev ? b : 0, E, e, b, c.w.feat, c.st);
+    return learnq_features(dprev, dstride, dprev ? b : 0, E, e, b, c.w.feat, c.w.level, false, c.st);
 }
 
 // The cached splits of T(:, k0:n) (rows) and T22 (columns), made now, outside
@@ -1040,7 +1042,7 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
         CK(fp64_iterate(c, k0, c.w.Y, 2));
     } else if (c.mode == MODE_TRACE) {
         CK(fp64_begin(c, i, k0));
-        CK(block_features(c, i, np, k0 > 0 ? c.w.rdiag : nullptr, 1));
+        CK(block_features(c, i, np, i > c.start_step ? c.w.rdiag : nullptr, 1));
         CK(trace_candidates(c, k0));
         if (c.tr_count < c.tr_max) {
             double cand[4 * 512];
@@ -1081,7 +1083,7 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
         }
         // the previous block's decay: the R diagonal of its panel QR, ready
         // before its small SVD (which keeps overlapping this step)
-        CK(block_features(c, i, np, k0 > 0 ? c.w.rdiag : nullptr, 1));
+        CK(block_features(c, i, np, i > c.start_step ? c.w.rdiag : nullptr, 1));
         CK(learnq_infer(c.have_model ? c.w.qmodel : nullptr, c.w.feat, c.q, c.w.qdev, c.w.qlog + i, c.st));
         if (!lowp) CK(prefetch_splits(c, k0));
         // every iteration up to q = 3 is queued; the kernels of iteration it
