@@ -79,6 +79,7 @@ struct Workspace {
     size_t oz_bytes;
     void* oz_rows;    // digit planes of T(:, k0:n) split by rows (kept for one step)
     void* oz_cols;    // digit planes of T22 split by columns (kept for one step)
+    size_t oz_rows_bytes;  // size of oz_rows (reused by the grouped U / V accumulation)
     double* svdp;     // FP32-preconditioned SVD: Q, Q', Gram, triu(R), R Q (w x w each), or null
     double* defer;    // reflectors and small factors kept for the deferred U / V accumulation
     size_t defer_elems;
@@ -243,6 +244,7 @@ Workspace carve(void* base, const Layout& L) {
     w.oz_bytes = L.off[29] - L.off[28];
     w.oz_rows = L.off[30] > L.off[29] ? (void*)(p + L.off[29]) : nullptr;
     w.oz_cols = L.off[31] > L.off[30] ? (void*)(p + L.off[30]) : nullptr;
+    w.oz_rows_bytes = L.off[30] - L.off[29];
     w.svdp = L.off[32] > L.off[31] ? (double*)(p + L.off[31]) : nullptr;
     w.defer = (double*)(p + L.off[32]);
     w.defer_elems = (L.off[33] - L.off[32]) / sizeof(double);
@@ -807,12 +809,89 @@ cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
 
 // X (len x cols, ld ldx) := (I - W Tf W^T) X with W (len x w, ld len) and
 // the upper triangular Tf (w x w) of a compact WY product Q = I - W Tf W^T.
+// Xs, X2s: w x cols scratch (default c.w.X, c.w.X2).
 cudaError_t apply_left(Ctx& c, const double* W, const double* Tf, double* X, int64_t ldx, int64_t len, int64_t cols,
-                       int w) {
+                       int w, double* Xs = nullptr, double* X2s = nullptr) {
     if (len <= 0 || cols <= 0) return cudaSuccess;
-    CK(gemm(c, "gemm_accumulate", true, false, w, cols, len, 1.0, W, len, X, ldx, 0.0, c.w.X, w));
-    CK(gemm(c, "gemm_accumulate_tf", false, false, w, cols, w, 1.0, Tf, w, c.w.X, w, 0.0, c.w.X2, w));
-    return gemm(c, "gemm_accumulate", false, false, len, cols, w, -1.0, W, len, c.w.X2, w, 1.0, X, ldx);
+    if (!Xs) Xs = c.w.X;
+    if (!X2s) X2s = c.w.X2;
+    CK(gemm(c, "gemm_accumulate", true, false, w, cols, len, 1.0, W, len, X, ldx, 0.0, Xs, w));
+    CK(gemm(c, "gemm_accumulate_tf", false, false, w, cols, w, 1.0, Tf, w, Xs, w, 0.0, X2s, w));
+    return gemm(c, "gemm_accumulate", false, false, len, cols, w, -1.0, W, len, X2s, w, 1.0, X, ldx);
+}
+
+// Grouped form of the deferred accumulation (emulated products only).  An
+// emulated product with K = b spends most of its time in the drain and the
+// FP64 epilogue, once per output element and product, rather than in the
+// MMAs.  The compact WY forms of up to kAccGroup consecutive steps are
+// therefore merged into one, Q_i Q_{i+1} ... = I - W T W^T with
+// W = [W_i, W_{i+1}, ...] (each W_j placed at its own first row k0_j - k0_i)
+// and T built step by step by the block rule of a product of two compact WY
+// forms, T = [[T_a, -T_a (W_a^T W_b) T_b], [0, T_b]] (Sec. 2.3): one update
+// with K = kAccGroup b replaces kAccGroup updates with K = b.  The group's
+// S factors act on its own diagonal blocks, which the later Q's of the group
+// do not touch, so they commute with those Q's and are written first.  The
+// scratch is carved from the cached-split buffer, unused once the
+// factorization loop has ended.
+constexpr int kAccGroup = 4;
+
+struct AccScratch {
+    double *W, *T, *G, *Y, *X, *X2;
+};
+
+bool acc_scratch(Ctx& c, int64_t nx, AccScratch* sc) {
+    if (!emulated_prec(c.prec) || c.w.oz_rows == nullptr) return false;
+    const size_t wg = (size_t)kAccGroup * c.b;
+    const size_t need = align_up(sizeof(double) * (size_t)nx * wg) * 3 + align_up(sizeof(double) * wg * wg) +
+                        2 * align_up(sizeof(double) * wg * (size_t)c.b);
+    if (need > c.w.oz_rows_bytes) return false;
+    char* p = (char*)c.w.oz_rows;
+    auto take = [&](size_t elems) {
+        double* q = (double*)p;
+        p += align_up(sizeof(double) * elems);
+        return q;
+    };
+    sc->W = take((size_t)nx * wg);
+    sc->X = take((size_t)nx * wg);
+    sc->X2 = take((size_t)nx * wg);
+    sc->T = take(wg * wg);
+    sc->G = take(wg * (size_t)c.b);
+    sc->Y = take(wg * (size_t)c.b);
+    c.oc = OzCache{-1};  // the cached splits are overwritten from here on
+    return true;
+}
+
+// Merged W (len0 x wsum, ld len0) and T (wsum x wsum, ld wsum) of steps
+// i0..i1 (consecutive, each with a transform) of the U (is_v false) or V
+// factor; k0 of step i0 is the group's first row.
+cudaError_t merge_wy(Ctx& c, const AccScratch& sc, int64_t nx, bool is_v, int64_t i0, int64_t i1, int* wsum_out) {
+    const int64_t k00 = c.steps[(size_t)i0].k0, len0 = nx - k00;
+    int wsum = 0;
+    for (int64_t j = i0; j <= i1; ++j) wsum += is_v ? c.b : c.steps[(size_t)j].w;
+    TraceScope ts("gemm_accumulate_merge", 0.0, 8.0 * (double)len0 * wsum, c.st);
+    CK(cudaMemsetAsync(sc.W, 0, sizeof(double) * (size_t)len0 * wsum, c.st));
+    CK(cudaMemsetAsync(sc.T, 0, sizeof(double) * (size_t)wsum * wsum, c.st));
+    int wacc = 0;
+    for (int64_t j = i0; j <= i1; ++j) {
+        const Ctx::Step& r = c.steps[(size_t)j];
+        const int wj = is_v ? c.b : r.w;
+        const int64_t off = r.k0 - k00, lenj = nx - r.k0;
+        const double* Wj = c.w.defer + (is_v ? r.wv : r.wu);
+        const double* Tj = c.w.defer + (is_v ? r.tv : r.tu);
+        CK(copy_matrix(Wj, lenj, sc.W + off + (int64_t)wacc * len0, len0, lenj, wj, c.st));
+        if (wacc > 0) {  // T(0:wacc, wacc:wacc+wj) = -T_acc (W_acc^T W_j) T_j
+            CK(gemm(c, "gemm_accumulate_merge", true, false, wacc, wj, lenj, 1.0, sc.W + off, len0, Wj, lenj, 0.0,
+                    sc.G, wacc));
+            CK(gemm(c, "gemm_accumulate_merge", false, false, wacc, wj, wacc, 1.0, sc.T, wsum, sc.G, wacc, 0.0, sc.Y,
+                    wacc));
+            CK(gemm(c, "gemm_accumulate_merge", false, false, wacc, wj, wj, -1.0, sc.Y, wacc, Tj, wj, 0.0,
+                    sc.T + (int64_t)wacc * wsum, wsum));
+        }
+        CK(copy_matrix(Tj, wj, sc.T + wacc + (int64_t)wacc * wsum, wsum, wj, wj, c.st));
+        wacc += wj;
+    }
+    *wsum_out = wsum;
+    return cudaSuccess;
 }
 
 // Deferred accumulation of the orthogonal factors (the backward order of
@@ -825,14 +904,30 @@ cudaError_t apply_left(Ctx& c, const double* W, const double* Tf, double* X, int
 // updating V at every step.
 cudaError_t accumulate(Ctx& c, double* X, int64_t nx, int64_t ldx, bool is_v) {
     CK(set_identity(X, nx, ldx, c.st));
-    for (int64_t i = (int64_t)c.steps.size() - 1; i >= 0; --i) {
-        const Ctx::Step& r = c.steps[(size_t)i];
-        double* Xb = X + r.k0 + r.k0 * ldx;
-        CK(copy_matrix(c.w.defer + (is_v ? r.vs : r.us), r.w, Xb, ldx, r.w, r.w, c.st));
-        if (is_v && !r.sketch) continue;
-        const int w = is_v ? c.b : r.w;
-        CK(apply_left(c, c.w.defer + (is_v ? r.wv : r.wu), c.w.defer + (is_v ? r.tv : r.tu), Xb, ldx, nx - r.k0,
-                      nx - r.k0, w));
+    AccScratch sc{};
+    const bool grouped = acc_scratch(c, nx, &sc);
+    auto has_q = [&](int64_t j) { return !is_v || c.steps[(size_t)j].sketch; };
+    for (int64_t i = (int64_t)c.steps.size() - 1; i >= 0;) {
+        int64_t i0 = i;  // the group is steps i0..i
+        if (grouped && has_q(i))
+            while (i0 > 0 && i - i0 + 1 < kAccGroup && has_q(i0 - 1)) --i0;
+        for (int64_t j = i; j >= i0; --j) {
+            const Ctx::Step& r = c.steps[(size_t)j];
+            CK(copy_matrix(c.w.defer + (is_v ? r.vs : r.us), r.w, X + r.k0 + r.k0 * ldx, ldx, r.w, r.w, c.st));
+        }
+        const Ctx::Step& r0 = c.steps[(size_t)i0];
+        double* Xb = X + r0.k0 + r0.k0 * ldx;
+        if (!has_q(i)) {
+        } else if (i0 == i) {
+            const int w = is_v ? c.b : r0.w;
+            CK(apply_left(c, c.w.defer + (is_v ? r0.wv : r0.wu), c.w.defer + (is_v ? r0.tv : r0.tu), Xb, ldx,
+                          nx - r0.k0, nx - r0.k0, w));
+        } else {
+            int wsum = 0;
+            CK(merge_wy(c, sc, nx, is_v, i0, i, &wsum));
+            CK(apply_left(c, sc.W, sc.T, Xb, ldx, nx - r0.k0, nx - r0.k0, wsum, sc.X, sc.X2));
+        }
+        i = i0 - 1;
     }
     return cudaSuccess;
 }
