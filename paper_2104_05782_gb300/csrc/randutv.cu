@@ -74,6 +74,7 @@ struct Workspace {
     double* rdiag;    // learned q / trace: the R diagonal of the last panel QR (w)
     double* sdiag;    // learned q / trace: |R_jj| of the compressed sketch (w)
     double* level;    // learned q / trace: the compressed sketch's norm, and the first block's (2)
+    double* W2;       // left update from the old split: W_V(b:, :) ((n' - b) x b), or null
     float* qmodel;    // network parameters on the device
     void* oz;         // digit slices and exponents of the emulated FP64 products
     size_t oz_bytes;
@@ -91,7 +92,7 @@ struct Workspace {
     int* qlog;        // learned mode: the q chosen at each sketch step (-1: none)
 };
 
-constexpr int kSlots = 37;
+constexpr int kSlots = 38;
 struct Layout {
     size_t off[kSlots];
     size_t total;
@@ -191,7 +192,8 @@ Layout make_layout(int64_t m, int64_t n, int b, int sms, int prec, bool qr_first
         emulated_prec(prec) ? 2 * oz_operand_bytes(mx, std::max<int64_t>(wmax, 128)) + 8192 : 0,  // side Ozaki
         sizeof(double) * (size_t)mx * wmax,                                             // side tmp
         sizeof(double) * part,                                                          // side partials
-        sizeof(int) * (size_t)(n / std::max(b, 1) + 2)};                                 // learned q per step
+        sizeof(int) * (size_t)(n / std::max(b, 1) + 2),                                  // learned q per step
+        emulated_prec(prec) ? sizeof(double) * (size_t)mx * wmax : 0};                  // W_V(b:, :)
     size_t o = 0;
     for (int i = 0; i < kSlots; ++i) {
         L.off[i] = o;
@@ -253,6 +255,7 @@ Workspace carve(void* base, const Layout& L) {
     w.tmp2 = (double*)(p + L.off[34]);
     w.part2 = (double*)(p + L.off[35]);
     w.qlog = (int*)(p + L.off[36]);
+    w.W2 = L.total > L.off[37] ? (double*)(p + L.off[37]) : nullptr;
     return w;
 }
 
@@ -382,6 +385,10 @@ struct Ctx {
     double *U, *T, *V;
     Workspace w;
     OzCache oc;
+    // left update of the current sketch step from the column split of T22
+    // made before the right update (left_from_old_split_prepare)
+    bool left_old = false;
+    OzOperand left_cols{};
     int sms;
     cudaStream_t st;
     // deferred U / V: what each block step left in w.defer
@@ -758,6 +765,45 @@ cudaError_t wait_applied(Ctx& c) {
     return cudaSuccess;
 }
 
+// Left update of a sketch step from the column split of T22 that the sketch
+// made before the right update (emulated products, small SVD on the side
+// stream).  With X2 = T(:, k0:n) W_V T_V and W_V = [W_1; W_2] (first b rows:
+// the panel's columns), the right-updated trailing block is
+// T22' = T22 - X2_b W_2^T (X2_b = X2(k0:m, :)), so the left update's
+// W_U^T T22' = (T22^T W_U - W_2 (W_U^T X2_b)^T)^T: the large product reads
+// the existing split of T22 instead of splitting T22' afresh, and only two
+// small products are added.  Both terms are separate products with their
+// own scales; the difference carries the absolute error of the right
+// update itself (a few units of rounding of T22).  Call before the right
+// update: it records the split and keeps W_2, which the panel QR overwrites.
+cudaError_t left_from_old_split_prepare(Ctx& c, int64_t k0) {
+    c.left_old = false;
+    const int64_t mp = c.m - k0, np = c.n - k0, nt = np - c.b;
+    if (!c.overlap || !emulated_prec(c.prec) || c.w.W2 == nullptr || nt < 16 || !oz_shape(c, np, c.b, mp))
+        return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    const OzOperand* ac = oz_cols_of(c, k0, &e);
+    CK(e);
+    c.left_cols = *ac;
+    CK(copy_matrix(c.w.W + c.b, np, c.w.W2, nt, nt, c.b, c.st));
+    c.left_old = true;
+    return cudaSuccess;
+}
+
+// T22' := Q_U^T T22' on T(k0:m, k0+w:n) by the formula above (W_U, T_U in
+// c.w.W, c.w.Tf; X2 in c.w.X2 from the right update).
+cudaError_t apply_left_old(Ctx& c, int64_t k0, int w) {
+    const int64_t m = c.m, mp = m - k0, nt = c.n - k0 - w, ldt = c.ldt;
+    if (nt <= 0 || mp <= 0) return cudaSuccess;
+    double* Y1 = c.w.G;  // nt x w
+    CK(oz_cached_product(c, "gemm_left", c.left_cols, w, nt, w, c.w.W, mp, Y1, nt));
+    CK(gemm(c, "gemm_left", true, false, w, w, mp, 1.0, c.w.W, mp, c.w.X2 + k0, m, 0.0, c.w.gram, w));
+    CK(gemm(c, "gemm_left_tf", false, true, nt, w, w, -1.0, c.w.W2, nt, c.w.gram, w, 1.0, Y1, nt));
+    CK(gemm(c, "gemm_left_tf", false, false, nt, w, w, 1.0, Y1, nt, c.w.Tf, w, 0.0, c.w.X, nt));
+    return gemm(c, "gemm_left", false, true, mp, nt, w, -1.0, c.w.W, mp, c.w.X, nt, 1.0, c.T + k0 + (k0 + w) * ldt,
+                ldt);
+}
+
 // Panel QR of T(k0:m, k0:k0+w), left update, small SVD and its application.
 cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
     const int64_t m = c.m, n = c.n, ldt = c.ldt;
@@ -775,7 +821,11 @@ cudaError_t panel_and_svd(Ctx& c, int64_t k0, int w) {
         CK(flush_pending(c));
         CK(svd_side(c, P, ldt, w));
         c.pending = (int64_t)c.steps.size() - 1;
-        CK(apply_left_t(c, T + k0 + (k0 + w) * ldt, ldt, mp, n - k0 - w, w));
+        if (c.left_old && w == c.b)
+            CK(apply_left_old(c, k0, w));
+        else
+            CK(apply_left_t(c, T + k0 + (k0 + w) * ldt, ldt, mp, n - k0 - w, w));
+        c.left_old = false;
         Ctx::Step& rec = c.steps.back();
         if (c.U) {  // U is accumulated backwards at the end from W_U, T_U, U_s
             CK(defer_put(c, c.w.W, mp, mp, w, &rec.wu));
@@ -842,8 +892,8 @@ struct AccScratch {
 bool acc_scratch(Ctx& c, int64_t nx, AccScratch* sc) {
     if (!emulated_prec(c.prec) || c.w.oz_rows == nullptr) return false;
     const size_t wg = (size_t)kAccGroup * c.b;
-    const size_t need = align_up(sizeof(double) * (size_t)nx * wg) * 3 + align_up(sizeof(double) * wg * wg) +
-                        2 * align_up(sizeof(double) * wg * (size_t)c.b);
+    const size_t need = align_up(sizeof(double) * (size_t)nx * wg) * 3 + 2 * align_up(sizeof(double) * wg * wg) +
+                        align_up(sizeof(double) * wg * (size_t)c.b);
     if (need > c.w.oz_rows_bytes) return false;
     char* p = (char*)c.w.oz_rows;
     auto take = [&](size_t elems) {
@@ -855,7 +905,7 @@ bool acc_scratch(Ctx& c, int64_t nx, AccScratch* sc) {
     sc->X = take((size_t)nx * wg);
     sc->X2 = take((size_t)nx * wg);
     sc->T = take(wg * wg);
-    sc->G = take(wg * (size_t)c.b);
+    sc->G = take(wg * wg);
     sc->Y = take(wg * (size_t)c.b);
     c.oc = OzCache{-1};  // the cached splits are overwritten from here on
     return true;
@@ -863,31 +913,40 @@ bool acc_scratch(Ctx& c, int64_t nx, AccScratch* sc) {
 
 // Merged W (len0 x wsum, ld len0) and T (wsum x wsum, ld wsum) of steps
 // i0..i1 (consecutive, each with a transform) of the U (is_v false) or V
-// factor; k0 of step i0 is the group's first row.
+// factor; k0 of step i0 is the group's first row.  Every block W_a^T W_b the
+// rule needs comes from one product, W(:, 0:wsum-w_last)^T W(:, w_0:wsum)
+// (its lower blocks are not used), which costs fewer launches than one
+// product per step.
 cudaError_t merge_wy(Ctx& c, const AccScratch& sc, int64_t nx, bool is_v, int64_t i0, int64_t i1, int* wsum_out) {
     const int64_t k00 = c.steps[(size_t)i0].k0, len0 = nx - k00;
+    auto width = [&](int64_t j) { return is_v ? c.b : c.steps[(size_t)j].w; };
     int wsum = 0;
-    for (int64_t j = i0; j <= i1; ++j) wsum += is_v ? c.b : c.steps[(size_t)j].w;
+    for (int64_t j = i0; j <= i1; ++j) wsum += width(j);
+    const int w0 = width(i0), wl = width(i1);
     TraceScope ts("gemm_accumulate_merge", 0.0, 8.0 * (double)len0 * wsum, c.st);
     CK(cudaMemsetAsync(sc.W, 0, sizeof(double) * (size_t)len0 * wsum, c.st));
     CK(cudaMemsetAsync(sc.T, 0, sizeof(double) * (size_t)wsum * wsum, c.st));
-    int wacc = 0;
+    int off = 0;
     for (int64_t j = i0; j <= i1; ++j) {
         const Ctx::Step& r = c.steps[(size_t)j];
-        const int wj = is_v ? c.b : r.w;
-        const int64_t off = r.k0 - k00, lenj = nx - r.k0;
-        const double* Wj = c.w.defer + (is_v ? r.wv : r.wu);
-        const double* Tj = c.w.defer + (is_v ? r.tv : r.tu);
-        CK(copy_matrix(Wj, lenj, sc.W + off + (int64_t)wacc * len0, len0, lenj, wj, c.st));
-        if (wacc > 0) {  // T(0:wacc, wacc:wacc+wj) = -T_acc (W_acc^T W_j) T_j
-            CK(gemm(c, "gemm_accumulate_merge", true, false, wacc, wj, lenj, 1.0, sc.W + off, len0, Wj, lenj, 0.0,
-                    sc.G, wacc));
-            CK(gemm(c, "gemm_accumulate_merge", false, false, wacc, wj, wacc, 1.0, sc.T, wsum, sc.G, wacc, 0.0, sc.Y,
-                    wacc));
-            CK(gemm(c, "gemm_accumulate_merge", false, false, wacc, wj, wj, -1.0, sc.Y, wacc, Tj, wj, 0.0,
-                    sc.T + (int64_t)wacc * wsum, wsum));
-        }
-        CK(copy_matrix(Tj, wj, sc.T + wacc + (int64_t)wacc * wsum, wsum, wj, wj, c.st));
+        const int wj = width(j);
+        const int64_t lenj = nx - r.k0;
+        CK(copy_matrix(c.w.defer + (is_v ? r.wv : r.wu), lenj, sc.W + (r.k0 - k00) + (int64_t)off * len0, len0, lenj,
+                       wj, c.st));
+        CK(copy_matrix(c.w.defer + (is_v ? r.tv : r.tu), wj, sc.T + off + (int64_t)off * wsum, wsum, wj, wj, c.st));
+        off += wj;
+    }
+    // Gc (wsum - wl) x (wsum - w0), ld wsum - wl: block (a, b) = W_a^T W_b
+    const int gr = wsum - wl, gc = wsum - w0;
+    CK(gemm(c, "gemm_accumulate_merge", true, false, gr, gc, len0, 1.0, sc.W, len0, sc.W + (int64_t)w0 * len0, len0,
+            0.0, sc.G, gr));
+    int wacc = w0;
+    for (int64_t j = i0 + 1; j <= i1; ++j) {  // T(0:wacc, wacc:wacc+wj) = -T_acc (W_acc^T W_j) T_j
+        const int wj = width(j);
+        const double* Gj = sc.G + (int64_t)(wacc - w0) * gr;  // rows 0:wacc of the column block of step j
+        CK(gemm(c, "gemm_accumulate_merge", false, false, wacc, wj, wacc, 1.0, sc.T, wsum, Gj, gr, 0.0, sc.Y, wacc));
+        CK(gemm(c, "gemm_accumulate_merge", false, false, wacc, wj, wj, -1.0, sc.Y, wacc,
+                sc.T + wacc + (int64_t)wacc * wsum, wsum, 0.0, sc.T + (int64_t)wacc * wsum, wsum));
         wacc += wj;
     }
     *wsum_out = wsum;
@@ -1193,6 +1252,7 @@ cudaError_t sketch_step(Ctx& c, int64_t i) {
         if (lowp) CK(lowp_finish(c, ls));
     }
     CK(factor_panel(c, c.w.Y, np, np, b));
+    CK(left_from_old_split_prepare(c, k0));
     CK(apply_right_T(c, k0, b));
     CK(flush_pending(c));  // the previous step's Us^T may now reach rows blk_{i-1}
     Ctx::Step rec{k0, b, true, 0, 0, 0, 0, 0, 0};
