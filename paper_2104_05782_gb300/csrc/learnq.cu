@@ -39,6 +39,15 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NI * NH, OFF_W2 = OFF_B1 + NH, OFF_B
               NPARAM = OFF_SD + NI;
 constexpr int NTRAIN = OFF_MU;  // trainable parameters (mu, sd are fixed)
 constexpr float kLearnqConfidence = 0.99f;
+// q = 0 is taken only for a block whose trailing matrix is below 1e-12 of the
+// whole (f[8] <= -12): its singular values sit at the rounding level of any
+// FP64 factorization of these sizes (n eps ||A|| ~ 1e-12 ||A|| at n = 16000).
+// Above it the choice is at least 1: q = 0 inside a cluster of equal singular
+// values leaves the cluster's directions in the trailing matrix at the size
+// of the gap that follows (sigma_small / sigma_cluster, against its cube for
+// q = 1), which distorts the blocks past the gap, while the training label
+// looks at the block's own diagonal only.
+constexpr float kLearnqNoiseLevel = -12.0f;
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_d(float x) {
@@ -298,6 +307,7 @@ __global__ void __launch_bounds__(NH) k_learnq_infer(const float* __restrict__ P
             break;
         }
     }
+    if (choice == 0 && !(f[8] <= kLearnqNoiseLevel)) choice = 1;
     *q = choice;
     if (qlog) *qlog = choice;
 }

@@ -79,7 +79,7 @@ def forcing_model(q):
     return p
 
 
-@pytest.mark.parametrize("q", [0, 2])
+@pytest.mark.parametrize("q", [1, 2])
 def test_learned_path_with_forcing_model_equals_fixed_q(rutv, q):
     A = synthetic.test_matrix(500, 400, "algebraic", 5, 6)
     m, n, b = 500, 400, 64
@@ -97,6 +97,34 @@ def test_learned_path_with_forcing_model_equals_fixed_q(rutv, q):
     nrm = np.linalg.norm(A)
     assert np.abs(host(T) - host(Tf)).max() <= 1e-10 * nrm
     assert np.abs(host(U) @ host(T) - host(Uf) @ host(Tf)).max() <= 1e-10 * nrm
+
+
+def test_forced_q0_only_at_the_noise_floor(rutv):
+    """A network that always answers q = 0 gets q = 0 only for blocks whose
+    trailing matrix is at the rounding level (the level feature f[8] at most
+    -12, i.e. ||T22||_F below 1e-12 of the first block's); above it the choice
+    is raised to 1.  On exp32 (sigma_i = 10^(-i/32), floored at 1e-15) the
+    first blocks are above the floor and the last ones at it."""
+    n, b = 1024, 64
+    A = synthetic.test_matrix(n, n, "exp32", 7, 8)
+    s = synthetic.spectrum("exp32", n)
+    T = rutv.colmajor_empty(n, n)
+    U = rutv.colmajor_empty(n, n)
+    V = rutv.colmajor_empty(n, n)
+    r, qu = rutv.randutv_factor_learnedq(n, n, dev(A), n, b, forcing_model(0), 5, U, T, V)
+    torch.cuda.synchronize()
+    assert r == 0
+    qu = [int(x) for x in qu]
+    assert qu[-1] == -1 and set(qu[:-1]) <= {0, 1}
+    # trailing Frobenius norm of the spectrum, relative to the whole
+    lvl = [np.sqrt(np.sum(s[i * b:] ** 2) / np.sum(s ** 2)) for i in range(len(qu) - 1)]
+    for i, x in enumerate(qu[:-1]):
+        if lvl[i] > 1e-10:
+            assert x == 1, (i, lvl[i], qu)
+        if lvl[i] < 1e-14:
+            assert x == 0, (i, lvl[i], qu)
+    nrm = np.linalg.norm(A)
+    assert np.linalg.norm(A - host(U) @ host(T) @ host(V).T) / nrm <= utv_bound(n)
 
 
 def test_no_model_falls_back_to_q2(rutv):
