@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "randUTV s/factorization & TFLOP/s at n=16000: mixed/learned-q vs FP64, % peak"
 # digit products per emulated FP64 product (8 digits, the pairs with s + t <= 7, 0-based)
+SIDE_STREAM_CLASSES = ("gemm_accumulate_merge", "gemm_svdapply")  # product classes run on the side stream
 OZ_PAIRS = 36
 DTYPES = {"fp64": "f64", "bf16": "f64+bf16-sketch", "fp16": "f64+fp16-sketch",
           "emul": "f64 (products emulated on bf16 tensor cores)",
@@ -520,10 +521,15 @@ def run_gb300(args, rank: int, world: int, local_rank: int):
     if sigma is not None:
         quality = diag_quality(d, sigma, b)
 
-    # dominant kernel: the FP64 products (class names "gemm_*"), all their launches
-    g_ms = sum(v["ms"] for k, v in trace.items() if k.startswith("gemm"))
-    g_fl = sum(v["flops"] for k, v in trace.items() if k.startswith("gemm"))
-    g_launch = sum(v["scopes"] for k, v in trace.items() if k.startswith("gemm"))
+    # dominant kernel: the FP64 products (class names "gemm_*") on the main
+    # stream.  The side stream's products (the small-SVD application and the
+    # merges of the U/V groups) run concurrently with main-stream products, so
+    # their event times include time the two streams share: they are left out
+    # (about 1% of the product flops).
+    main = {k: v for k, v in trace.items() if k.startswith("gemm") and k not in SIDE_STREAM_CLASSES}
+    g_ms = sum(v["ms"] for v in main.values())
+    g_fl = sum(v["flops"] for v in main.values())
+    g_launch = sum(v["scopes"] for v in main.values())
     tot_ms = sum(v["ms"] for v in trace.values())
     if args.prec in ("emul", "emul_bf16"):
         # k_oz_gemm executes OZ_PAIRS BF16 digit products per FP64 product

@@ -601,12 +601,12 @@ unsigned oz_grid(int64_t total) { return (unsigned)std::max<int64_t>(1, std::min
 int64_t oz_ldq(int64_t K) { return (K + 63) / 64 * 64; }
 
 // split-K factor: slices of whole 128-deep chunks until there are about
-// four jobs per SM; partials (FP64) need splits * M * N doubles
+// eight jobs per SM (a shorter tail of the last wave); partials (FP64) need splits * M * N doubles
 int oz_splits(int64_t M, int64_t N, int64_t K, int sms, size_t p_bytes) {
     const int64_t tiles = cdiv(M, OZ_TM) * cdiv(N, OZ_TN);
     const int64_t chunks = cdiv(cdiv(K, OZ_TK), OZ_CHUNK);
     int64_t s = 1;
-    if (tiles < 4LL * sms) s = cdiv(4LL * sms, tiles);
+    if (tiles < 8LL * sms) s = cdiv(8LL * sms, tiles);
     if (s > chunks) s = chunks;
     if (s > 64) s = 64;
     const int64_t fit = (int64_t)(p_bytes / (sizeof(double) * (size_t)M * (size_t)N));

@@ -329,6 +329,8 @@ struct SideStream {
     cudaEvent_t panel = nullptr, right = nullptr;     // main -> side: panel factored, right update done
     cudaEvent_t applied = nullptr;                    // side -> main: small SVD applied to T
     cudaEvent_t svd_done = nullptr;                   // side -> main: small SVD computed (D ready)
+    cudaEvent_t merged[2] = {nullptr, nullptr};       // side -> main: a U/V group's WY form merged
+    cudaEvent_t freed[2] = {nullptr, nullptr};        // main -> side: that merge buffer applied
 };
 std::mutex g_side_mu;
 std::unordered_map<int, SideStream> g_side;
@@ -347,6 +349,10 @@ cudaError_t side_stream(SideStream** out) {
         if ((e = cudaEventCreateWithFlags(&s.right, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&s.applied, cudaEventDisableTiming)) != cudaSuccess) return e;
         if ((e = cudaEventCreateWithFlags(&s.svd_done, cudaEventDisableTiming)) != cudaSuccess) return e;
+        for (int k = 0; k < 2; ++k) {
+            if ((e = cudaEventCreateWithFlags(&s.merged[k], cudaEventDisableTiming)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&s.freed[k], cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
     }
     *out = &s;
     return cudaSuccess;
@@ -882,18 +888,24 @@ cudaError_t apply_left(Ctx& c, const double* W, const double* Tf, double* X, int
 // S factors act on its own diagonal blocks, which the later Q's of the group
 // do not touch, so they commute with those Q's and are written first.  The
 // scratch is carved from the cached-split buffer, unused once the
-// factorization loop has ended.
+// factorization loop has ended; the merges run on the side stream.
 constexpr int kAccGroup = 4;
 
 struct AccScratch {
-    double *W, *T, *G, *Y, *X, *X2;
+    double *Wb[2], *Tb[2];  // merged W and T, one per group in flight
+    double *G, *Y, *X, *X2;
+    void* oz;               // emulated-product work of the merges (side stream)
+    size_t oz_bytes;
 };
 
 bool acc_scratch(Ctx& c, int64_t nx, AccScratch* sc) {
     if (!emulated_prec(c.prec) || c.w.oz_rows == nullptr) return false;
     const size_t wg = (size_t)kAccGroup * c.b;
-    const size_t need = align_up(sizeof(double) * (size_t)nx * wg) * 3 + 2 * align_up(sizeof(double) * wg * wg) +
-                        align_up(sizeof(double) * wg * (size_t)c.b);
+    // the merges' own emulated-product work: two split operands of up to
+    // wg x nx and the split-K partials of a wg x wg product
+    const size_t ozb = 2 * oz_operand_bytes((int64_t)wg, nx) + sizeof(double) * wg * wg * 64 + 4096;
+    const size_t need = align_up(sizeof(double) * (size_t)nx * wg) * 4 + 3 * align_up(sizeof(double) * wg * wg) +
+                        align_up(sizeof(double) * wg * (size_t)c.b) + align_up(ozb);
     if (need > c.w.oz_rows_bytes) return false;
     char* p = (char*)c.w.oz_rows;
     auto take = [&](size_t elems) {
@@ -901,52 +913,58 @@ bool acc_scratch(Ctx& c, int64_t nx, AccScratch* sc) {
         p += align_up(sizeof(double) * elems);
         return q;
     };
-    sc->W = take((size_t)nx * wg);
+    sc->Wb[0] = take((size_t)nx * wg);
+    sc->Wb[1] = take((size_t)nx * wg);
     sc->X = take((size_t)nx * wg);
     sc->X2 = take((size_t)nx * wg);
-    sc->T = take(wg * wg);
+    sc->Tb[0] = take(wg * wg);
+    sc->Tb[1] = take(wg * wg);
     sc->G = take(wg * wg);
     sc->Y = take(wg * (size_t)c.b);
+    sc->oz = (void*)p;
+    sc->oz_bytes = ozb;
     c.oc = OzCache{-1};  // the cached splits are overwritten from here on
     return true;
 }
 
 // Merged W (len0 x wsum, ld len0) and T (wsum x wsum, ld wsum) of steps
 // i0..i1 (consecutive, each with a transform) of the U (is_v false) or V
-// factor; k0 of step i0 is the group's first row.  Every block W_a^T W_b the
-// rule needs comes from one product, W(:, 0:wsum-w_last)^T W(:, w_0:wsum)
-// (its lower blocks are not used), which costs fewer launches than one
-// product per step.
-cudaError_t merge_wy(Ctx& c, const AccScratch& sc, int64_t nx, bool is_v, int64_t i0, int64_t i1, int* wsum_out) {
+// factor, into Wm, Tm; k0 of step i0 is the group's first row.  Every block
+// W_a^T W_b the rule needs comes from one product,
+// W(:, 0:wsum-w_last)^T W(:, w_0:wsum) (its lower blocks are not used).
+// c supplies the steps and the deferred store, cx the stream and the work
+// buffers of the products (the side stream's, when the merge runs there).
+cudaError_t merge_wy(const Ctx& c, Ctx& cx, double* Wm, double* Tm, double* Gs, double* Ys, int64_t nx, bool is_v,
+                     int64_t i0, int64_t i1, int* wsum_out) {
     const int64_t k00 = c.steps[(size_t)i0].k0, len0 = nx - k00;
     auto width = [&](int64_t j) { return is_v ? c.b : c.steps[(size_t)j].w; };
     int wsum = 0;
     for (int64_t j = i0; j <= i1; ++j) wsum += width(j);
     const int w0 = width(i0), wl = width(i1);
-    TraceScope ts("gemm_accumulate_merge", 0.0, 8.0 * (double)len0 * wsum, c.st);
-    CK(cudaMemsetAsync(sc.W, 0, sizeof(double) * (size_t)len0 * wsum, c.st));
-    CK(cudaMemsetAsync(sc.T, 0, sizeof(double) * (size_t)wsum * wsum, c.st));
+    TraceScope ts("gemm_accumulate_merge", 0.0, 8.0 * (double)len0 * wsum, cx.st);
+    CK(cudaMemsetAsync(Wm, 0, sizeof(double) * (size_t)len0 * wsum, cx.st));
+    CK(cudaMemsetAsync(Tm, 0, sizeof(double) * (size_t)wsum * wsum, cx.st));
     int off = 0;
     for (int64_t j = i0; j <= i1; ++j) {
         const Ctx::Step& r = c.steps[(size_t)j];
         const int wj = width(j);
         const int64_t lenj = nx - r.k0;
-        CK(copy_matrix(c.w.defer + (is_v ? r.wv : r.wu), lenj, sc.W + (r.k0 - k00) + (int64_t)off * len0, len0, lenj,
-                       wj, c.st));
-        CK(copy_matrix(c.w.defer + (is_v ? r.tv : r.tu), wj, sc.T + off + (int64_t)off * wsum, wsum, wj, wj, c.st));
+        CK(copy_matrix(c.w.defer + (is_v ? r.wv : r.wu), lenj, Wm + (r.k0 - k00) + (int64_t)off * len0, len0, lenj,
+                       wj, cx.st));
+        CK(copy_matrix(c.w.defer + (is_v ? r.tv : r.tu), wj, Tm + off + (int64_t)off * wsum, wsum, wj, wj, cx.st));
         off += wj;
     }
     // Gc (wsum - wl) x (wsum - w0), ld wsum - wl: block (a, b) = W_a^T W_b
     const int gr = wsum - wl, gc = wsum - w0;
-    CK(gemm(c, "gemm_accumulate_merge", true, false, gr, gc, len0, 1.0, sc.W, len0, sc.W + (int64_t)w0 * len0, len0,
-            0.0, sc.G, gr));
+    CK(gemm(cx, "gemm_accumulate_merge", true, false, gr, gc, len0, 1.0, Wm, len0, Wm + (int64_t)w0 * len0, len0,
+            0.0, Gs, gr));
     int wacc = w0;
     for (int64_t j = i0 + 1; j <= i1; ++j) {  // T(0:wacc, wacc:wacc+wj) = -T_acc (W_acc^T W_j) T_j
         const int wj = width(j);
-        const double* Gj = sc.G + (int64_t)(wacc - w0) * gr;  // rows 0:wacc of the column block of step j
-        CK(gemm(c, "gemm_accumulate_merge", false, false, wacc, wj, wacc, 1.0, sc.T, wsum, Gj, gr, 0.0, sc.Y, wacc));
-        CK(gemm(c, "gemm_accumulate_merge", false, false, wacc, wj, wj, -1.0, sc.Y, wacc,
-                sc.T + wacc + (int64_t)wacc * wsum, wsum, 0.0, sc.T + (int64_t)wacc * wsum, wsum));
+        const double* Gj = Gs + (int64_t)(wacc - w0) * gr;  // rows 0:wacc of the column block of step j
+        CK(gemm(cx, "gemm_accumulate_merge", false, false, wacc, wj, wacc, 1.0, Tm, wsum, Gj, gr, 0.0, Ys, wacc));
+        CK(gemm(cx, "gemm_accumulate_merge", false, false, wacc, wj, wj, -1.0, Ys, wacc, Tm + wacc + (int64_t)wacc * wsum,
+                wsum, 0.0, Tm + (int64_t)wacc * wsum, wsum));
         wacc += wj;
     }
     *wsum_out = wsum;
@@ -966,27 +984,65 @@ cudaError_t accumulate(Ctx& c, double* X, int64_t nx, int64_t ldx, bool is_v) {
     AccScratch sc{};
     const bool grouped = acc_scratch(c, nx, &sc);
     auto has_q = [&](int64_t j) { return !is_v || c.steps[(size_t)j].sketch; };
+    struct Grp {
+        int64_t i0, i1;
+    };
+    std::vector<Grp> groups;  // from the last step back
     for (int64_t i = (int64_t)c.steps.size() - 1; i >= 0;) {
-        int64_t i0 = i;  // the group is steps i0..i
+        int64_t i0 = i;
         if (grouped && has_q(i))
             while (i0 > 0 && i - i0 + 1 < kAccGroup && has_q(i0 - 1)) --i0;
-        for (int64_t j = i; j >= i0; --j) {
+        groups.push_back(Grp{i0, i});
+        i = i0 - 1;
+    }
+    // The merges run on the side stream one group ahead of the updates, each
+    // into one of two buffers: the merge of the next group overlaps the
+    // update of this one.  The side stream first waits for everything the
+    // main stream has queued (the deferred store is complete).
+    std::vector<size_t> merged_groups;
+    for (size_t k = 0; k < groups.size(); ++k)
+        if (groups[k].i1 > groups[k].i0) merged_groups.push_back(k);
+    SideStream* ss = nullptr;
+    Ctx c2;
+    std::vector<int> wsums(groups.size(), 0);
+    auto launch_merge = [&](size_t t) -> cudaError_t {  // t-th merged group, buffer t % 2
+        const Grp& g = groups[merged_groups[t]];
+        const int bsel = (int)(t % 2);
+        CK(cudaStreamWaitEvent(ss->st, ss->freed[bsel], 0));  // no wait before the buffer's first use
+        CK(merge_wy(c, c2, sc.Wb[bsel], sc.Tb[bsel], sc.G, sc.Y, nx, is_v, g.i0, g.i1, &wsums[merged_groups[t]]));
+        return cudaEventRecord(ss->merged[bsel], ss->st);
+    };
+    if (!merged_groups.empty()) {
+        CK(side_stream(&ss));
+        c2 = side_ctx(c, ss->st);
+        c2.w.oz = sc.oz;
+        c2.w.oz_bytes = sc.oz_bytes;
+        CK(cudaEventRecord(ss->right, c.st));
+        CK(cudaStreamWaitEvent(ss->st, ss->right, 0));
+        CK(launch_merge(0));
+    }
+    size_t t = 0;  // merged groups applied so far
+    for (size_t k = 0; k < groups.size(); ++k) {
+        const Grp& g = groups[k];
+        for (int64_t j = g.i1; j >= g.i0; --j) {
             const Ctx::Step& r = c.steps[(size_t)j];
             CK(copy_matrix(c.w.defer + (is_v ? r.vs : r.us), r.w, X + r.k0 + r.k0 * ldx, ldx, r.w, r.w, c.st));
         }
-        const Ctx::Step& r0 = c.steps[(size_t)i0];
+        const Ctx::Step& r0 = c.steps[(size_t)g.i0];
         double* Xb = X + r0.k0 + r0.k0 * ldx;
-        if (!has_q(i)) {
-        } else if (i0 == i) {
+        if (!has_q(g.i1)) {
+        } else if (g.i0 == g.i1) {
             const int w = is_v ? c.b : r0.w;
             CK(apply_left(c, c.w.defer + (is_v ? r0.wv : r0.wu), c.w.defer + (is_v ? r0.tv : r0.tu), Xb, ldx,
                           nx - r0.k0, nx - r0.k0, w));
         } else {
-            int wsum = 0;
-            CK(merge_wy(c, sc, nx, is_v, i0, i, &wsum));
-            CK(apply_left(c, sc.W, sc.T, Xb, ldx, nx - r0.k0, nx - r0.k0, wsum, sc.X, sc.X2));
+            if (t + 1 < merged_groups.size()) CK(launch_merge(t + 1));
+            const int bsel = (int)(t % 2);
+            CK(cudaStreamWaitEvent(c.st, ss->merged[bsel], 0));
+            CK(apply_left(c, sc.Wb[bsel], sc.Tb[bsel], Xb, ldx, nx - r0.k0, nx - r0.k0, wsums[k], sc.X, sc.X2));
+            CK(cudaEventRecord(ss->freed[bsel], c.st));
+            ++t;
         }
-        i = i0 - 1;
     }
     return cudaSuccess;
 }
