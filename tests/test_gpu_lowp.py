@@ -52,6 +52,13 @@ def test_lowp_exact_and_quality(rutv, prec_name, m, n, b, q, kind):
     _, T64, _ = run(rutv, A, b, q, rutv.RANDUTV_FP64)
     s = np.linalg.svd(A, compute_uv=False)
     keep = s > 1e3 * 2.0 ** -53 * s[0]          # ratios below the FP64 noise floor are not meaningful
+    if kind == "gap":
+        # the indices past the gap inside the block that straddles it: the q = 2
+        # sketch weighs those directions at (1e-3)^5 of the cluster's, far below
+        # a 16-bit sketch's rounding (and below FP64's), so their T_ii are set
+        # by rounding in every precision
+        k_gap = n // 10
+        keep[k_gap:(k_gap // b + 1) * b] = False
     r_lp = np.diag(T)[keep] / s[keep]
     r_64 = np.diag(T64)[keep] / s[keep]
     dev = np.abs(r_lp / r_64 - 1.0)
@@ -62,7 +69,15 @@ def test_lowp_exact_and_quality(rutv, prec_name, m, n, b, q, kind):
     frac = ok.mean()
     print("%s %s: max dev %.3g at %d, %.4f of indices within 5%% (or better), median dev %.2e"
           % (prec_name, kind, dev.max(), int(np.argmax(dev)), frac, np.median(dev)))
-    assert frac >= 0.98
+    # a 16-bit sketch fixes its subspace to about 2^-8 (BF16) or 2^-11 (FP16)
+    # and T_ii / sigma_i of randUTV spreads by a few percent in every
+    # precision, most at the first or last index of a block; on the gap
+    # spectrum the directions past the gap that the straddling block's 16-bit
+    # sketch did not separate stay in the trailing matrix and move the next
+    # block's first indices by up to 15% (FP16, 1024^2).  So: every index
+    # within 15% of the FP64 ratio (or closer to 1), all but 1% within 5%.
+    assert ((dev <= 0.15) | (np.abs(np.log(r_lp)) <= np.abs(np.log(r_64)))).all()
+    assert frac >= 0.99
 
 
 def test_lowp_deterministic(rutv):
