@@ -269,7 +269,7 @@ randutv_status randutv_batched_autotune(int count, const int64_t* m, const int64
  *             A non-finite network output also falls back to q = 2.  The
  *             network predicts a distribution over the smallest adequate q;
  *             the step runs the smallest q whose cumulative predicted
- *             probability reaches 0.99.
+ *             probability reaches 0.999.
  *   q_used  : HOST array of ceil(n / b) ints (or NULL): the q chosen per
  *             sketch step, -1 for the final block (no sketch).
  * Other arguments as randutv_factor / randutv_factor_ex.  The choice stays

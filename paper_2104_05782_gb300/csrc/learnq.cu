@@ -38,7 +38,7 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NI * NH, OFF_W2 = OFF_B1 + NH, OFF_B
               OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NH * NO, OFF_MU = OFF_B3 + NO, OFF_SD = OFF_MU + NI,
               NPARAM = OFF_SD + NI;
 constexpr int NTRAIN = OFF_MU;  // trainable parameters (mu, sd are fixed)
-constexpr float kLearnqConfidence = 0.99f;
+constexpr float kLearnqConfidence = 0.999f;
 // q = 0 is taken only for a block whose trailing matrix is below 1e-12 of the
 // whole (f[8] <= -12): its singular values sit at the rounding level of any
 // FP64 factorization of these sizes (n eps ||A|| ~ 1e-12 ||A|| at n = 16000).
@@ -131,55 +131,103 @@ __global__ void k_learnq_features(const double* __restrict__ dprev, int64_t dstr
 }
 
 // |R_jj| of the Householder QR of E (e x w, FP64, ld lde; e <= 256, w <= 128)
-// for the learned-q features, in FP32 in one block: E is scaled by its
-// largest entry and held in shared memory; warp 0 builds each reflector
-// (e <= 256 rows: eight per lane and a shuffle sum), then every warp applies it
-// to its share of the remaining columns.  Ratios |R_jj| / |R_00| come out to
-// FP32 accuracy and saturate near 1e-7, where the remaining columns are
-// rounding; the features clip there consistently in training and use.
+// for the learned-q features, in FP32 in one block of 32 warps.  E is held
+// in registers: warp q owns columns q, q + 32, q + 64, q + 96 and lane l rows
+// l, l + 32, ..., l + 224 of each.  E is scaled by a power of two (from its
+// largest exponent) and cut to FP32 with integer instructions (truncation),
+// so no FP64 instruction touches its 32768 entries.  Step j: the warp owning
+// column j builds the reflector (dlarfg rule) from its registers and writes
+// v to shared memory (two buffers by the parity of j, so one block barrier
+// per step); every warp then applies it to its own columns right of j, with
+// v read once per step.  Ratios |R_jj| / |R_00| come out to FP32 accuracy and
+// saturate near 1e-7, where the remaining columns are rounding; the features
+// clip there consistently in training and use.  *level = ||E||_F (an FP32
+// sum of the scaled squares).
 constexpr int FQR_THREADS = 1024;
+constexpr int FQR_RP = 8;  // rows per lane (e <= 256)
+constexpr int FQR_CP = 4;  // columns per warp (w <= 128)
+
+// x 2^-s as FP32 by truncation, built from the FP64 bit pattern; values
+// below the FP32 normal range give 0.
+__device__ __forceinline__ float f64_to_f32_scaled(double x, int s) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int be = (int)((u >> 52) & 0x7FF);
+    if (be == 0) return 0.0f;
+    const int fe = be - 1023 - s + 127;
+    if (fe <= 0) return 0.0f;
+    const uint32_t bits = ((uint32_t)(u >> 63) << 31) | ((uint32_t)min(fe, 254) << 23) |
+                          (uint32_t)((u >> 29) & 0x7FFFFFull);
+    return __uint_as_float(bits);
+}
+
 __global__ void __launch_bounds__(FQR_THREADS) k_feature_rdiag32(const double* __restrict__ E, int64_t lde, int e, int w,
                                                                  double* __restrict__ rdiag, double* __restrict__ level) {
-    extern __shared__ float fa[];  // e x w, column stride ld = e + 1
-    __shared__ float s_tau;
-    __shared__ double s_max[32], s_ss[32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ld = e + 1;
-    double mx = 0.0, ss = 0.0;  // largest |E| and the sum of squares (the level), fixed order
-    for (int t = tid; t < e * w; t += FQR_THREADS) {
-        const double x = E[(t % e) + (int64_t)(t / e) * lde];
-        mx = fmax(mx, fabs(x));
-        ss = fma(x, x, ss);
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    ss = warp_sum(ss);
-    if (lane == 0) {
-        s_max[warp] = mx;
-        s_ss[warp] = ss;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double m = 0.0, q = 0.0;
-        for (int k = 0; k < FQR_THREADS / 32; ++k) {
-            m = fmax(m, s_max[k]);
-            q += s_ss[k];
+    __shared__ float vbuf[2][FQR_RP * 32];
+    __shared__ float s_tau[2];
+    __shared__ int s_be[32];
+    __shared__ float s_ss[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // the largest biased exponent of E (integer max of the bit patterns)
+    int mbe = 0;
+#pragma unroll
+    for (int q = 0; q < FQR_CP; ++q) {
+        const int c = warp + 32 * q;
+#pragma unroll
+        for (int k = 0; k < FQR_RP; ++k) {
+            const int r = lane + 32 * k;
+            if (c < w && r < e) {
+                const unsigned long long u = (unsigned long long)__double_as_longlong(E[r + (int64_t)c * lde]);
+                mbe = max(mbe, (int)((u >> 52) & 0x7FF));
+            }
         }
-        s_max[0] = m;
-        level[0] = sqrt(q);
     }
+    for (int o = 16; o > 0; o >>= 1) mbe = max(mbe, __shfl_xor_sync(0xffffffffu, mbe, o));
+    if (lane == 0) s_be[warp] = mbe;
     __syncthreads();
-    const double scale = s_max[0] > 0.0 ? 1.0 / s_max[0] : 1.0;
-    for (int t = tid; t < e * w; t += FQR_THREADS) {
-        const int r = t % e, c = t / e;
-        fa[r + ld * c] = (float)(E[r + (int64_t)c * lde] * scale);
+    int gbe = 0;
+    for (int k = 0; k < 32; ++k) gbe = max(gbe, s_be[k]);
+    const int sc = (gbe == 0) ? 0 : gbe - 1023;  // |E| / 2^sc < 2
+    float a[FQR_CP][FQR_RP];
+    float ss = 0.0f;
+#pragma unroll
+    for (int q = 0; q < FQR_CP; ++q) {
+        const int c = warp + 32 * q;
+#pragma unroll
+        for (int k = 0; k < FQR_RP; ++k) {
+            const int r = lane + 32 * k;
+            a[q][k] = (c < w && r < e) ? f64_to_f32_scaled(E[r + (int64_t)c * lde], sc) : 0.0f;
+            ss = fmaf(a[q][k], a[q][k], ss);
+        }
     }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) s_ss[warp] = ss;
     __syncthreads();
-    for (int j = 0; j < w && j < e; ++j) {
-        if (warp == 0) {  // the reflector of column j (dlarfg rule), v stored in place
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int k = 0; k < 32; ++k) t += s_ss[k];
+        level[0] = ldexp(sqrt((double)t), sc);
+    }
+    const int steps = min(w, e);
+    for (int j = 0; j < steps; ++j) {
+        const int p = j & 1;
+        const int qj = j >> 5;
+        if (warp == (j & 31)) {  // the owner of column j builds its reflector
+            float x[FQR_RP];
+#pragma unroll
+            for (int q = 0; q < FQR_CP; ++q)
+                if (q == qj)
+#pragma unroll
+                    for (int k = 0; k < FQR_RP; ++k) x[k] = a[q][k];
             float xi2 = 0.0f;
-            for (int r = j + 1 + lane; r < e; r += 32) xi2 = fmaf(fa[r + ld * j], fa[r + ld * j], xi2);
+#pragma unroll
+            for (int k = 0; k < FQR_RP; ++k)
+                if (lane + 32 * k > j) xi2 = fmaf(x[k], x[k], xi2);
             for (int o = 16; o > 0; o >>= 1) xi2 += __shfl_xor_sync(0xffffffffu, xi2, o);
-            const float alpha = fa[j + ld * j];
+            float alpha = 0.0f;
+#pragma unroll
+            for (int k = 0; k < FQR_RP; ++k)
+                if (lane + 32 * k == j) alpha = x[k];
+            alpha = __shfl_sync(0xffffffffu, alpha, j & 31);
             float beta = alpha, tau = 0.0f, inv = 0.0f;
             if (xi2 > 0.0f) {
                 const float h = sqrtf(fmaf(alpha, alpha, xi2));
@@ -187,24 +235,43 @@ __global__ void __launch_bounds__(FQR_THREADS) k_feature_rdiag32(const double* _
                 tau = (beta - alpha) / beta;
                 inv = 1.0f / (alpha - beta);
             }
-            for (int r = j + 1 + lane; r < e; r += 32) fa[r + ld * j] *= inv;
+#pragma unroll
+            for (int k = 0; k < FQR_RP; ++k) {
+                const int r = lane + 32 * k;
+                const float v = (r > j) ? x[k] * inv : (r == j ? 1.0f : 0.0f);
+                vbuf[p][r] = v;
+                x[k] = (r > j) ? v : (r == j ? beta : x[k]);
+            }
+#pragma unroll
+            for (int q = 0; q < FQR_CP; ++q)
+                if (q == qj)
+#pragma unroll
+                    for (int k = 0; k < FQR_RP; ++k) a[q][k] = x[k];
             if (lane == 0) {
                 rdiag[j] = fabs((double)beta);
-                s_tau = tau;
+                s_tau[p] = tau;
             }
         }
         __syncthreads();
-        const float tau = s_tau;
-        if (tau != 0.0f)
-            for (int c = j + 1 + warp; c < w; c += FQR_THREADS / 32) {  // column c -= tau v (v^T column c)
-                float d = 0.0f;
-                for (int r = j + 1 + lane; r < e; r += 32) d = fmaf(fa[r + ld * j], fa[r + ld * c], d);
-                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                d = tau * (d + fa[j + ld * c]);
-                if (lane == 0) fa[j + ld * c] -= d;
-                for (int r = j + 1 + lane; r < e; r += 32) fa[r + ld * c] = fmaf(-d, fa[r + ld * j], fa[r + ld * c]);
+        const float tau = s_tau[p];
+        if (tau != 0.0f) {
+            float v[FQR_RP];
+#pragma unroll
+            for (int k = 0; k < FQR_RP; ++k) v[k] = vbuf[p][lane + 32 * k];
+#pragma unroll
+            for (int q = 0; q < FQR_CP; ++q) {
+                const int c = warp + 32 * q;
+                if (c > j && c < w) {  // column c -= tau v (v^T column c), warp-uniform
+                    float d = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < FQR_RP; ++k) d = fmaf(v[k], a[q][k], d);
+                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                    d *= tau;
+#pragma unroll
+                    for (int k = 0; k < FQR_RP; ++k) a[q][k] = fmaf(-d, v[k], a[q][k]);
+                }
             }
-        __syncthreads();
+        }
     }
 }
 
@@ -422,15 +489,7 @@ cudaError_t countsketch(const double* Y, int64_t ldy, int64_t L, int w, int e, u
 cudaError_t feature_rdiag(const double* E, int64_t lde, int e, int w, double* rdiag, double* level,
                           cudaStream_t st) {
     if (e > 256 || w > 128 || e < 1 || w < 1) return cudaErrorInvalidValue;
-    const size_t shm = sizeof(float) * (size_t)(e + 1) * w;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t err = cudaFuncSetAttribute(k_feature_rdiag32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(sizeof(float) * 257 * 128));
-        if (err != cudaSuccess) return err;
-        configured = true;
-    }
-    k_feature_rdiag32<<<1, FQR_THREADS, shm, st>>>(E, lde, e, w, rdiag, level);
+    k_feature_rdiag32<<<1, FQR_THREADS, 0, st>>>(E, lde, e, w, rdiag, level);
     trace_count(1);
     return cudaGetLastError();
 }
