@@ -43,7 +43,7 @@ constexpr int kMaxChunk = 4096;   // rows per block (shared-memory bound)
 // contiguous (pc[g] for block g), so the tpc lanes of a column read
 // consecutive words, and each lane issues its loads in batches of kBatch
 // before adding, so that a batch costs one L2 round trip.
-constexpr int kBatch = 16;
+constexpr int kBatch = 20;
 __device__ __forceinline__ double split_colsum(const double* __restrict__ pc, int G, bool active, int sub, int tpc) {
     double s = 0.0;
     if (active) {
